@@ -1,0 +1,320 @@
+"""Benchmark: the full 77,169-neuron microcircuit on one GB300.
+
+One bench "step" = one persistent launch that simulates 1 s of biological
+time (10,000 time steps of 0.1 ms) of the full microcircuit (~3e8 synapses).
+The default run (warmup 3, steps 10) times 10 s of biological time, the
+paper's run length, after 3 s of warm-up that absorb the initial transient.
+
+Printed JSON line (rank 0):
+  value            synaptic events / s (device-timed, CUDA events on the
+                   library's stream), whole job over all ranks
+  real_time_factor wall time / biological time (< 1: faster than real time)
+  e2e              same metric through the public C ABI with the spike
+                   raster read back to host memory every step
+  roofline         the step kernel's algorithmic bytes (4 B per synaptic
+                   event: one packed synaptic word) / its launch time, over
+                   the measured HBM copy bandwidth
+  cpu_baseline     the CPU oracle timed on a bounded sample of the same
+                   workload on this host
+
+--impl reference times the CPU oracle itself (the reference arm).
+Multi-GPU (torchrun, --gpus N): N independent replicas, one per GPU.
+"""
+import argparse
+import json
+import os
+import signal
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "real-time factor and synaptic events/s (full microcircuit, 1 GB300); % HBM roofline"
+UNIT = "synaptic events/s"
+STEPS_PER_BENCH_STEP = 10000          # 1 s of biological time at dt = 0.1 ms
+BYTES_PER_EVENT = 4                   # one packed synaptic word read per event
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k] == "Active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])),
+                "sm_max_mhz": float(max(r[1] for r in rows)), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(cfg, n_threads_build, skip_steps, sample_steps):
+    """Time the CPU oracle's step loop on a bounded sample of the workload."""
+    import oracle
+    t0 = time.time()
+    net = oracle.Network(cfg, n_threads=n_threads_build)
+    build_s = time.time() - t0
+    sim = oracle.Simulation(net)
+    sim.run(skip_steps)
+    c0 = sim.counters()
+    t1 = time.perf_counter()
+    sim.run(sample_steps)
+    dt = time.perf_counter() - t1
+    c1 = sim.counters()
+    events = c1["events"] - c0["events"]
+    bio = sample_steps * cfg["dt"] * 1e-3
+    return {"value": events / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "steps %d..%d of the full microcircuit (seed %d), %.3f s biological, "
+                      "single-threaded step loop; network built untimed with %d threads in %.1f s"
+                      % (skip_steps, skip_steps + sample_steps, cfg["seed"], bio,
+                         n_threads_build, build_s),
+            "real_time_factor": dt / bio, "seconds": dt}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, as it stands, on this host's cores."""
+    import workload
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cfg = workload.microcircuit(args.scale)
+    import oracle
+    nthreads = os.cpu_count() or 1
+    t0 = time.time()
+    net = oracle.Network(cfg, n_threads=nthreads)
+    build_s = time.time() - t0
+    sim = oracle.Simulation(net)
+    chunk = args.ref_chunk
+    for _ in range(args.warmup):
+        sim.run(chunk)
+    c0 = sim.counters()
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.run(chunk)
+    dt = time.perf_counter() - t1
+    c1 = sim.counters()
+    events = c1["events"] - c0["events"]
+    value = events / dt
+    bio = args.steps * chunk * cfg["dt"] * 1e-3
+    sample = ("each step %d time steps (%.1f ms biological) of the full microcircuit after "
+              "%d warm-up steps; single-threaded oracle step loop; network built untimed "
+              "with %d threads in %.1f s" % (chunk, chunk * cfg["dt"], args.warmup, nthreads,
+                                             build_s))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/i32",
+            "data": "synthetic", "real_time_factor": dt / bio,
+            "config": {"workload": "full microcircuit, 77,169 LIF neurons, ~3e8 synapses, "
+                                   "Poisson background, dt 0.1 ms",
+                       "scale": args.scale, "seed": cfg["seed"],
+                       "time_steps_per_step": chunk},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1909_08665_gb300 as pkg
+    import workload
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    cfg = workload.microcircuit(args.scale, seed=12345 + rank)
+    chunk = STEPS_PER_BENCH_STEP
+    t_build = time.time()
+    net = pkg.Microcircuit(cfg, stream=stream)
+    build_s = time.time() - t_build
+    info = net.info()
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        net.step(chunk)
+    net.sync()
+    net.read_spikes_into(np.zeros(1 << 22, np.uint32), np.zeros(1 << 22, np.uint32))
+
+    # -------- device-timed region: K launches, inputs (1.2 GB rows) > L2 --------
+    c0 = net.counters()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        t_all0.record(stream)
+        for k in range(args.steps):
+            starts[k].record(stream)
+            net.step(chunk)
+            ends[k].record(stream)
+        t_all1.record(stream)
+        barrier()
+    net.sync()
+    c1 = net.counters()
+    total_ms = t_all0.elapsed_time(t_all1)
+    per_launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    events = c1["events"] - c0["events"]
+    spikes = c1["spikes"] - c0["spikes"]
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        e = torch.tensor([float(events)], device=dev, dtype=torch.float64)
+        dist.all_reduce(e)
+        events_all = float(e.item())
+    else:
+        events_all = float(events)
+    value = events_all / (total_ms * 1e-3)
+    bio_s = args.steps * chunk * cfg["dt"] * 1e-3
+    rtf = (total_ms * 1e-3) / bio_s
+
+    # -------- end to end through the C ABI: raster read to host each step --------
+    cap = 1 << 24
+    h_steps = torch.empty(cap, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    h_ids = torch.empty(cap, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    net.read_spikes_into(h_steps, h_ids)
+    barrier()
+    e0 = net.counters()["events"]
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.steps):
+        net.step(chunk)
+        n = net.read_spikes_into(h_steps, h_ids)
+        d2h += 8 * n + 8 * 3
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_events = net.counters()["events"] - e0
+    e2e_value = e2e_events * ws / e2e_s
+
+    hbm_peak, peak_kind = load_peaks()
+    avg_launch_s = float(np.mean(per_launch_ms)) * 1e-3
+    achieved = BYTES_PER_EVENT * (events / args.steps) / avg_launch_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/i32", "data": "synthetic",
+        "real_time_factor": rtf,
+        "config": {"workload": "full microcircuit, 77,169 LIF neurons, %d synapses, Poisson "
+                               "background, dt 0.1 ms; 1 step = 10,000 time steps (1 s biological)"
+                               % info["n_synapses"],
+                   "scale": args.scale, "seed": cfg["seed"], "time_steps_per_step": chunk,
+                   "l2": "no flush: synapse rows (%.2f GB) exceed the 129 MB L2"
+                         % (info["n_synapses"] * 4 / 1e9),
+                   "n_part": info["n_part"], "ring_in_shared": info["ring_in_shared"],
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "spikes_per_time_step": spikes / (args.steps * chunk),
+        "events_per_time_step": events / (args.steps * chunk),
+        "us_per_time_step": total_ms * 1e3 / (args.steps * chunk),
+        "build_s": build_s,
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": d2h // max(args.steps, 1),
+                "real_time_factor": e2e_s / bio_s},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "peak_kind": peak_kind, "kernel": "k_step (persistent step kernel)"},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, os.cpu_count() or 1, args.cpu_skip,
+                                            args.cpu_steps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--cpu-skip", type=int, default=500)
+    ap.add_argument("--cpu-steps", type=int, default=4000)
+    ap.add_argument("--ref-chunk", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

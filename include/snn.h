@@ -1,0 +1,210 @@
+/*
+ * snn.h -- C ABI of the GB300 library for the 0.1 ms time-stepped simulation
+ * of the cortical microcircuit (Rhodes et al., "Real-Time Cortical Simulation
+ * on Neuromorphic Hardware": Sec. 2.1 model and Eq. 1, Sec. 3.1.2 synaptic
+ * matrix and ring buffers, Sec. 3.1.3 per-step processing).
+ *
+ * Conventions for every entry point
+ *  - Return value: SNN_OK (0) or one of the SNN_ERR_* codes below; nothing
+ *    is thrown across the ABI.  snn_last_error() returns a thread-local,
+ *    human-readable message for the last failing call on this thread.
+ *  - Pointers named *_host are host memory owned by the caller; they are read
+ *    or written before the call returns.  The library owns every device
+ *    allocation it makes and frees it in snn_destroy().
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Device work of a network is issued on that stream only.
+ *  - The library needs an sm_103a GPU; on any other device snn_create()
+ *    fails with SNN_ERR_UNSUPPORTED.  There is no CPU fallback.
+ *
+ * Model (Sec. 2.1, Eq. 1, read as tau_m du/dt = -u + R I, dI/dt = -I/tau_syn
+ * + sum_j w_j delta(t - t_j), u = V - E_L), per step t and neuron i:
+ *   1. acc = ring[t mod D][i]; ring[t mod D][i] = 0          (int32, 1/256 pA)
+ *   2. Poisson background: acc += k w_ext, k ~ Poisson(nu_bg K_ext dt)
+ *   3. if refr > 0: refr -= 1, u = 0; else u = P22 u + P21 I (+ P20 I_DC)
+ *   4. I = P11 I + acc / 256                                  (fp32)
+ *   5. if u > theta: spike, u = 0, refr = n_ref
+ *   6. each spike of neuron j adds wtab[pop(i)][pop(j)][code] to
+ *      ring[(t + delay) mod D][i] for every synapse (i, delay, code) of row j.
+ * Integer accumulation makes every result independent of summation order,
+ * so spike rasters are bit-exact and reproducible.
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SNN_MAX_POP 8
+#define SNN_WCODES 128          /* weight codes per projection */
+#define SNN_RING_DEPTH 64       /* delay slots per neuron: delays 1..63 steps */
+#define SNN_MAX_NEURONS 524288  /* 19-bit target index in a synaptic word */
+
+enum {
+    SNN_OK = 0,
+    SNN_ERR_INVALID = 1,      /* bad argument or configuration */
+    SNN_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    SNN_ERR_OOM = 3,          /* device allocation failed */
+    SNN_ERR_TIMEOUT = 4,      /* a grid-barrier wait exceeded its time limit */
+    SNN_ERR_OVERFLOW = 5,     /* spike raster capacity exceeded (spikes lost) */
+    SNN_ERR_UNSUPPORTED = 6   /* device is not sm_103 or too small */
+};
+
+/*
+ * Network and model parameters.  Field for field the same quantities the
+ * paper's use case defines (Sec. 2.1): population sizes, connection
+ * probabilities p[target][source], normally distributed weights (pA) and
+ * delays (ms), Poisson background (K_ext x nu_bg, Sec. 3.1.3) or DC input,
+ * and the neuron constants of Eq. 1.
+ */
+typedef struct snn_config {
+    int32_t n_pop;                               /* 1..8 populations */
+    int32_t pop_size[SNN_MAX_POP];               /* neurons per population */
+    int32_t pop_exc[SNN_MAX_POP];                /* 1 excitatory, 0 inhibitory */
+    double conn_prob[SNN_MAX_POP][SNN_MAX_POP];  /* [target][source] */
+    double conn_scale;                           /* multiplies every probability */
+    double w_mean[SNN_MAX_POP][SNN_MAX_POP];     /* pA, signed, [target][source] */
+    double w_sd[SNN_MAX_POP][SNN_MAX_POP];       /* pA */
+    double w_scale;                              /* multiplies every weight */
+    double proj_scale[SNN_MAX_POP][SNN_MAX_POP]; /* per-projection weight factor */
+    double d_mean[SNN_MAX_POP];                  /* ms, by source population */
+    double d_sd[SNN_MAX_POP];                    /* ms */
+    double k_ext[SNN_MAX_POP];                   /* background in-degree */
+    double nu_bg;                                /* Hz, background rate */
+    double w_ext;                                /* pA, background weight */
+    double i_dc[SNN_MAX_POP];                    /* pA, DC input (input_mode 1) */
+    int32_t input_mode;                          /* 0 Poisson, 1 DC */
+    double tau_m, c_m, tau_syn, t_ref, theta, dt;/* ms, pF, ms, ms, mV, ms */
+    double u0_lo, u0_hi;                         /* default initial u range, mV */
+    int32_t ring_depth;                          /* must be SNN_RING_DEPTH */
+} snn_config;
+
+/* Execution options; a NULL pointer means all defaults. */
+typedef struct snn_options {
+    int32_t n_part;           /* partitions (= CTAs of the step kernel); 0 auto */
+    int32_t inject_fault;     /* 0 normally.  1: partition 0 withholds its
+                                 grid-barrier arrivals, so the other waits run
+                                 out after timeout_s and snn_sync() returns
+                                 SNN_ERR_TIMEOUT (tests of the failure path;
+                                 every wait is bounded, nothing hangs) */
+    int64_t raster_capacity;  /* spikes buffered on the device; 0 auto (64 Mi) */
+    double timeout_s;         /* limit of one grid-barrier wait; 0 = 2 s */
+} snn_options;
+
+typedef struct snn_info {
+    int64_t n_neurons;
+    int64_t n_synapses;
+    int32_t n_part;           /* partitions of the neuron range */
+    int32_t threads;          /* threads per CTA of the step kernel */
+    int32_t neurons_per_thread;
+    int32_t ring_in_shared;   /* 1: ring buffers live in shared memory */
+    int32_t max_part_neurons; /* largest partition */
+    int32_t n_ref;            /* refractory steps */
+    float propagators[4];     /* P22, P21, P11, P20 as used (fp32) */
+    int32_t wext_q;           /* background weight, 1/256 pA */
+    int32_t shared_bytes;     /* dynamic shared memory of the step kernel */
+} snn_info;
+
+typedef struct snn_net snn_net;
+
+/*
+ * snn_create -- build the network from `seed` on the device and set the
+ * initial state (Sec. 2.1: probabilistic connectivity, normal weights and
+ * delays; Sec. 4.1: initial conditions).
+ *   cfg      host, read only.
+ *   seed     Philox4x32-10 key for connectivity, weights, delays, background
+ *            and the default initial potentials.
+ *   opt      host or NULL.
+ *   u0_host  host, n_neurons floats (mV above rest) or NULL for the default
+ *            uniform draw on [u0_lo, u0_hi).
+ *   stream   cudaStream_t of all later work of this network.
+ *   out      receives the handle.
+ * Errors: SNN_ERR_INVALID (config), SNN_ERR_UNSUPPORTED (device),
+ * SNN_ERR_OOM, SNN_ERR_CUDA.  Blocks until the network is built.
+ */
+int snn_create(const snn_config* cfg, uint64_t seed, const snn_options* opt,
+               const float* u0_host, void* stream, snn_net** out);
+
+/*
+ * snn_create_from_rows -- like snn_create, but with a caller-given synaptic
+ * matrix (Sec. 3.1.2: one row per presynaptic neuron) instead of a generated
+ * one.  Rows: row_ptr_host[n+1] (uint64 offsets), words_host[nnz] packed as
+ * target (bits 0..18) | delay in steps (bits 19..24, 1..63) | weight code
+ * (bits 25..31); targets ascending within a row.  wtab_host[8*8*128] int32
+ * weights in 1/256 pA, index (target_pop*8 + source_pop)*128 + code.
+ */
+int snn_create_from_rows(const snn_config* cfg, uint64_t seed, const snn_options* opt,
+                         const uint64_t* row_ptr_host, const uint32_t* words_host,
+                         const int32_t* wtab_host, const float* u0_host, void* stream,
+                         snn_net** out);
+
+/*
+ * snn_step -- advance the simulation by n_steps time steps of dt (Sec. 3.1.3:
+ * every step updates all neurons, then delivers all spikes).  Asynchronous on
+ * the network's stream; n_steps >= 0.  Spikes are appended to the device
+ * raster.  Errors found on the device are reported by snn_sync().
+ */
+int snn_step(snn_net* net, int64_t n_steps);
+
+/* snn_sync -- wait for the stream; returns SNN_OK, SNN_ERR_TIMEOUT if a
+ * barrier wait gave up (state undefined), SNN_ERR_OVERFLOW if the raster
+ * overflowed, or SNN_ERR_CUDA. */
+int snn_sync(snn_net* net);
+
+/*
+ * snn_read_spikes -- drain the recorded spikes (Sec. 3.1.2: output spike
+ * times of all neurons are recorded) into steps_host[cap], ids_host[cap];
+ * *n receives the count copied.  Order is unspecified (sort if needed).
+ * Synchronises the stream.  SNN_ERR_OVERFLOW if spikes were lost on the
+ * device or cap is too small (the first cap are returned).
+ */
+int snn_read_spikes(snn_net* net, uint32_t* steps_host, uint32_t* ids_host, int64_t cap,
+                    int64_t* n);
+
+/* snn_raster_size -- number of recorded spikes waiting to be read (the
+ * capacity snn_read_spikes needs); synchronises the stream. */
+int snn_raster_size(snn_net* net, int64_t* n);
+
+/* snn_read_state -- copy u (mV), I_syn (pA) and refractory counters of all
+ * neurons into host arrays of n_neurons elements; any pointer may be NULL. */
+int snn_read_state(snn_net* net, float* u_host, float* i_syn_host, int32_t* refr_host);
+
+/* snn_read_ring -- copy the ring buffers into ring_host[64 * n_neurons],
+ * slot-major ([slot][neuron], slot = step mod 64), int32 in 1/256 pA. */
+int snn_read_ring(snn_net* net, int32_t* ring_host);
+
+/* snn_counters -- steps simulated, spikes emitted and synaptic events
+ * delivered (one spike reaching one synapse, Sec. 3.3), since creation. */
+int snn_counters(snn_net* net, int64_t* step, uint64_t* spikes, uint64_t* events);
+
+/* snn_get_info -- sizes and launch configuration. */
+int snn_get_info(snn_net* net, snn_info* info);
+
+/* snn_export_network -- copy the synaptic matrix: row_ptr_host[n+1],
+ * words_host[n_synapses] (format of snn_create_from_rows; ascending targets),
+ * wtab_host[8*8*128].  Any pointer may be NULL. */
+int snn_export_network(snn_net* net, uint64_t* row_ptr_host, uint32_t* words_host,
+                       int32_t* wtab_host);
+
+/*
+ * snn_deliver -- deliver one arbitrary spike list into the ring buffers, as
+ * step 6 does for the spikes of step t (Sec. 3.1.2: row fetch, word decode,
+ * buffer add).  spikes_dev: device array of n_spikes neuron ids (duplicates
+ * allowed).  tiling 0: one warp per spike; 1: one CTA per spike row.
+ * Asynchronous on the network's stream; adds to the existing ring content.
+ */
+int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int64_t t,
+                int32_t tiling);
+
+/* snn_destroy -- free all device memory of the network (synchronises). */
+int snn_destroy(snn_net* net);
+
+const char* snn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

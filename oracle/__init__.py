@@ -135,6 +135,8 @@ def lib():
                                   P(C.c_uint8), P(C.c_uint8), C.c_int64]
         L.orc_net_row.restype = C.c_int64
         L.orc_net_free.argtypes = [C.c_void_p]
+        L.orc_deliver.argtypes = [C.c_void_p, P(OrcConfig), P(C.c_int32), C.c_int64, C.c_int64,
+                                  P(C.c_int64)]
         L.orc_sim_create.argtypes = [C.c_void_p, P(OrcConfig), C.c_uint64, P(C.c_float)]
         L.orc_sim_create.restype = C.c_void_p
         L.orc_sim_run.argtypes = [C.c_void_p, C.c_int64]
@@ -257,6 +259,18 @@ class Network:
         lib().orc_net_export(self._h, _ptr(rp, C.c_int64), _ptr(tg, C.c_int32),
                              _ptr(dl, C.c_uint8), _ptr(wc, C.c_uint8))
         return rp, tg[:self.nnz], dl[:self.nnz], wc[:self.nnz]
+
+    def deliver(self, spikes, t: int, ring: np.ndarray | None = None) -> np.ndarray:
+        """Add the rows of ``spikes`` (spikes of step ``t``) into ``ring``
+        ([D][n] int64, zeros if omitted) and return it."""
+        D = int(self.cfg["ring_depth"])
+        if ring is None:
+            ring = np.zeros((D, self.n), np.int64)
+        ring = np.ascontiguousarray(ring, np.int64)
+        sp = np.ascontiguousarray(spikes, np.int32)
+        lib().orc_deliver(self._h, C.byref(self._c), _ptr(sp, C.c_int32), int(sp.size), int(t),
+                          _ptr(ring, C.c_int64))
+        return ring
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -556,6 +556,26 @@ static void sim_step(orc_sim* s)
     s->step += 1;
 }
 
+/* Step 6 alone for an arbitrary spike list of step t: every word of every
+ * listed row adds its weight to ring slot (t + delay) mod D of its target
+ * (Sec. 3.1.2).  ring is [D][n], int64. */
+void orc_deliver(const orc_net* net, const orc_config* c, const int32_t* spikes, int64_t n_spikes,
+                 int64_t t, int64_t* ring)
+{
+    const int64_t n = net->n;
+    const int D = c->ring_depth;
+    for (int64_t k = 0; k < n_spikes; ++k) {
+        int64_t j = spikes[k];
+        int q = pop_of(net->pop_start, net->n_pop, j);
+        for (int64_t e = net->row_ptr[j]; e < net->row_ptr[j + 1]; ++e) {
+            int64_t i = net->tgt[e];
+            int p = pop_of(net->pop_start, net->n_pop, i);
+            ring[((t + net->delay[e]) % D) * n + i] +=
+                net->wtab[(p * ORC_MAX_POP + q) * ORC_WCODES + net->wcode[e]];
+        }
+    }
+}
+
 int64_t orc_sim_run(orc_sim* s, int64_t n_steps)
 {
     int64_t before = s->rs_n;

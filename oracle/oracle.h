@@ -63,6 +63,8 @@ void orc_net_export(const orc_net* n, int64_t* row_ptr, int32_t* tgt, uint8_t* d
 int64_t orc_net_row(const orc_config* c, uint64_t seed, int64_t j, int32_t* tgt,
                     uint8_t* delay, uint8_t* wcode, int64_t cap);
 void orc_net_free(orc_net* n);
+void orc_deliver(const orc_net* net, const orc_config* c, const int32_t* spikes, int64_t n_spikes,
+                 int64_t t, int64_t* ring);
 
 /* simulation */
 orc_sim* orc_sim_create(const orc_net* net, const orc_config* c, uint64_t seed,

@@ -1,0 +1,293 @@
+"""Python binding of the GB300 cortical-microcircuit library (``include/snn.h``).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of ``libsnn_gb300.so``.  The functions keep the C names
+(``snn_create``, ``snn_step`` ...); :class:`Microcircuit` wraps one network
+handle.  There is no CPU fallback: importing the binding without the built
+library, or calling it without a CUDA device, raises.
+
+Device memory and streams may come from PyTorch: pass
+``torch.cuda.current_stream().cuda_stream`` as the stream, and device
+tensors' ``data_ptr()`` where the ABI takes device pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsnn_gb300.so")
+MAX_POP = 8
+WCODES = 128
+RING_DEPTH = 64
+
+SNN_OK, SNN_ERR_INVALID, SNN_ERR_CUDA, SNN_ERR_OOM = 0, 1, 2, 3
+SNN_ERR_TIMEOUT, SNN_ERR_OVERFLOW, SNN_ERR_UNSUPPORTED = 4, 5, 6
+_ERR_NAMES = {1: "INVALID", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "OVERFLOW", 6: "UNSUPPORTED"}
+
+
+class SnnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("SNN_ERR_%s: %s" % (_ERR_NAMES.get(code, code), msg))
+        self.code = code
+
+
+class SnnConfig(C.Structure):
+    _fields_ = [
+        ("n_pop", C.c_int32),
+        ("pop_size", C.c_int32 * MAX_POP),
+        ("pop_exc", C.c_int32 * MAX_POP),
+        ("conn_prob", (C.c_double * MAX_POP) * MAX_POP),
+        ("conn_scale", C.c_double),
+        ("w_mean", (C.c_double * MAX_POP) * MAX_POP),
+        ("w_sd", (C.c_double * MAX_POP) * MAX_POP),
+        ("w_scale", C.c_double),
+        ("proj_scale", (C.c_double * MAX_POP) * MAX_POP),
+        ("d_mean", C.c_double * MAX_POP),
+        ("d_sd", C.c_double * MAX_POP),
+        ("k_ext", C.c_double * MAX_POP),
+        ("nu_bg", C.c_double),
+        ("w_ext", C.c_double),
+        ("i_dc", C.c_double * MAX_POP),
+        ("input_mode", C.c_int32),
+        ("tau_m", C.c_double),
+        ("c_m", C.c_double),
+        ("tau_syn", C.c_double),
+        ("t_ref", C.c_double),
+        ("theta", C.c_double),
+        ("dt", C.c_double),
+        ("u0_lo", C.c_double),
+        ("u0_hi", C.c_double),
+        ("ring_depth", C.c_int32),
+    ]
+
+
+class SnnOptions(C.Structure):
+    _fields_ = [("n_part", C.c_int32), ("inject_fault", C.c_int32),
+                ("raster_capacity", C.c_int64), ("timeout_s", C.c_double)]
+
+
+class SnnInfo(C.Structure):
+    _fields_ = [("n_neurons", C.c_int64), ("n_synapses", C.c_int64), ("n_part", C.c_int32),
+                ("threads", C.c_int32), ("neurons_per_thread", C.c_int32),
+                ("ring_in_shared", C.c_int32), ("max_part_neurons", C.c_int32),
+                ("n_ref", C.c_int32), ("propagators", C.c_float * 4), ("wext_q", C.c_int32),
+                ("shared_bytes", C.c_int32)]
+
+
+EXPORTED = ["snn_create", "snn_create_from_rows", "snn_step", "snn_sync", "snn_read_spikes",
+            "snn_raster_size", "snn_read_state", "snn_read_ring", "snn_counters", "snn_get_info",
+            "snn_export_network", "snn_deliver", "snn_destroy", "snn_last_error"]
+
+_lib = None
+
+
+def lib():
+    """Load ``libsnn_gb300.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libsnn_gb300.so is not built; run "
+                              "python -c 'import __graft_entry__ as g; g.build()'")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER
+        vp = C.c_void_p
+        L.snn_create.argtypes = [P(SnnConfig), C.c_uint64, P(SnnOptions), P(C.c_float), vp, P(vp)]
+        L.snn_create_from_rows.argtypes = [P(SnnConfig), C.c_uint64, P(SnnOptions),
+                                           P(C.c_uint64), P(C.c_uint32), P(C.c_int32),
+                                           P(C.c_float), vp, P(vp)]
+        L.snn_step.argtypes = [vp, C.c_int64]
+        L.snn_sync.argtypes = [vp]
+        L.snn_read_spikes.argtypes = [vp, P(C.c_uint32), P(C.c_uint32), C.c_int64, P(C.c_int64)]
+        L.snn_raster_size.argtypes = [vp, P(C.c_int64)]
+        L.snn_read_state.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_int32)]
+        L.snn_read_ring.argtypes = [vp, P(C.c_int32)]
+        L.snn_counters.argtypes = [vp, P(C.c_int64), P(C.c_uint64), P(C.c_uint64)]
+        L.snn_get_info.argtypes = [vp, P(SnnInfo)]
+        L.snn_export_network.argtypes = [vp, P(C.c_uint64), P(C.c_uint32), P(C.c_int32)]
+        L.snn_deliver.argtypes = [vp, vp, C.c_int32, C.c_int64, C.c_int32]
+        L.snn_destroy.argtypes = [vp]
+        L.snn_last_error.restype = C.c_char_p
+        for name in EXPORTED:
+            if name != "snn_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != SNN_OK:
+        raise SnnError(rc, lib().snn_last_error().decode())
+
+
+def _ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ctype))
+
+
+def make_config(cfg: dict) -> SnnConfig:
+    """Fill an ``snn_config`` from a configuration dictionary."""
+    c = SnnConfig()
+    npop = len(cfg["pop_sizes"])
+    if not 1 <= npop <= MAX_POP:
+        raise ValueError("1..8 populations")
+    c.n_pop = npop
+    for p in range(npop):
+        c.pop_size[p] = int(cfg["pop_sizes"][p])
+        c.pop_exc[p] = int(cfg["pop_exc"][p])
+        c.d_mean[p] = float(cfg["d_mean"][p])
+        c.d_sd[p] = float(cfg["d_sd"][p])
+        c.k_ext[p] = float(cfg["k_ext"][p])
+        c.i_dc[p] = float(cfg["i_dc"][p])
+        for q in range(npop):
+            c.conn_prob[p][q] = float(cfg["conn_prob"][p][q])
+            c.w_mean[p][q] = float(cfg["w_mean"][p][q])
+            c.w_sd[p][q] = float(cfg["w_sd"][p][q])
+            c.proj_scale[p][q] = float(cfg["proj_scale"][p][q])
+    c.conn_scale = float(cfg["conn_scale"])
+    c.w_scale = float(cfg["w_scale"])
+    c.nu_bg = float(cfg["nu_bg"])
+    c.w_ext = float(cfg["w_ext"])
+    c.input_mode = int(cfg["input_mode"])
+    for k in ("tau_m", "c_m", "tau_syn", "t_ref", "theta", "dt", "u0_lo", "u0_hi"):
+        setattr(c, k, float(cfg[k]))
+    c.ring_depth = int(cfg["ring_depth"])
+    return c
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)          # torch.cuda.Stream
+
+
+class Microcircuit:
+    """One simulated network on the current CUDA device."""
+
+    def __init__(self, cfg: dict, seed: int | None = None, u0=None, n_part: int = 0,
+                 raster_capacity: int = 0, timeout_s: float = 0.0, stream=None,
+                 rows: dict | None = None, inject_fault: int = 0):
+        self.cfg = cfg
+        self.seed = int(cfg["seed"] if seed is None else seed)
+        self._c = make_config(cfg)
+        self._o = SnnOptions(int(n_part), int(inject_fault), int(raster_capacity),
+                             float(timeout_s))
+        self.n = int(sum(cfg["pop_sizes"]))
+        self._u0 = None if u0 is None else np.ascontiguousarray(u0, np.float32)
+        if self._u0 is not None and self._u0.size != self.n:
+            raise ValueError("u0 must have one value per neuron")
+        self.stream = _stream_handle(stream)
+        h = C.c_void_p()
+        L = lib()
+        if rows is None:
+            rc = L.snn_create(C.byref(self._c), self.seed, C.byref(self._o),
+                              _ptr(self._u0, C.c_float), self.stream, C.byref(h))
+        else:
+            rp = np.ascontiguousarray(rows["row_ptr"], np.uint64)
+            wd = np.ascontiguousarray(rows["words"], np.uint32)
+            wt = np.ascontiguousarray(rows["wtab"], np.int32).reshape(-1)
+            rc = L.snn_create_from_rows(C.byref(self._c), self.seed, C.byref(self._o),
+                                        _ptr(rp, C.c_uint64), _ptr(wd, C.c_uint32),
+                                        _ptr(wt, C.c_int32), _ptr(self._u0, C.c_float),
+                                        self.stream, C.byref(h))
+        _check(rc)
+        self._h = h
+
+    # -- stepping ------------------------------------------------------------
+    def step(self, n_steps: int):
+        _check(lib().snn_step(self._h, int(n_steps)))
+
+    def sync(self):
+        _check(lib().snn_sync(self._h))
+
+    def deliver(self, spikes_dev_ptr: int, n_spikes: int, t: int, tiling: int = 0):
+        _check(lib().snn_deliver(self._h, C.c_void_p(int(spikes_dev_ptr)), int(n_spikes),
+                                 int(t), int(tiling)))
+
+    # -- reads ---------------------------------------------------------------
+    def info(self) -> dict:
+        i = SnnInfo()
+        _check(lib().snn_get_info(self._h, C.byref(i)))
+        return {k: (list(getattr(i, k)) if k == "propagators" else getattr(i, k))
+                for k, _ in SnnInfo._fields_}
+
+    def read_spikes(self, cap: int | None = None):
+        """Drain the device raster; returns (steps, ids) sorted by (step, id)."""
+        if cap is None:
+            cap = max(1, self.raster_size())
+        st = np.zeros(cap, np.uint32)
+        ids = np.zeros(cap, np.uint32)
+        n = C.c_int64()
+        _check(lib().snn_read_spikes(self._h, _ptr(st, C.c_uint32), _ptr(ids, C.c_uint32),
+                                     int(cap), C.byref(n)))
+        st, ids = st[:n.value], ids[:n.value]
+        order = np.lexsort((ids, st))
+        return st[order].astype(np.int64), ids[order].astype(np.int64)
+
+    def raster_size(self) -> int:
+        n = C.c_int64()
+        _check(lib().snn_raster_size(self._h, C.byref(n)))
+        return n.value
+
+    def read_spikes_into(self, steps_buf: np.ndarray, ids_buf: np.ndarray) -> int:
+        """Drain the raster into caller-provided uint32 host buffers (unsorted)."""
+        n = C.c_int64()
+        _check(lib().snn_read_spikes(self._h, _ptr(steps_buf, C.c_uint32),
+                                     _ptr(ids_buf, C.c_uint32), int(steps_buf.size),
+                                     C.byref(n)))
+        return n.value
+
+    def state(self):
+        u = np.zeros(self.n, np.float32)
+        i = np.zeros(self.n, np.float32)
+        r = np.zeros(self.n, np.int32)
+        _check(lib().snn_read_state(self._h, _ptr(u, C.c_float), _ptr(i, C.c_float),
+                                    _ptr(r, C.c_int32)))
+        return u, i, r
+
+    def ring(self):
+        out = np.zeros(RING_DEPTH * self.n, np.int32)
+        _check(lib().snn_read_ring(self._h, _ptr(out, C.c_int32)))
+        return out.reshape(RING_DEPTH, self.n)
+
+    def counters(self) -> dict:
+        s, a, b = C.c_int64(), C.c_uint64(), C.c_uint64()
+        _check(lib().snn_counters(self._h, C.byref(s), C.byref(a), C.byref(b)))
+        return {"step": s.value, "spikes": a.value, "events": b.value}
+
+    def export_network(self):
+        inf = self.info()
+        rp = np.zeros(self.n + 1, np.uint64)
+        wd = np.zeros(max(int(inf["n_synapses"]), 1), np.uint32)
+        wt = np.zeros(MAX_POP * MAX_POP * WCODES, np.int32)
+        _check(lib().snn_export_network(self._h, _ptr(rp, C.c_uint64), _ptr(wd, C.c_uint32),
+                                        _ptr(wt, C.c_int32)))
+        return rp, wd[:int(inf["n_synapses"])], wt.reshape(MAX_POP, MAX_POP, WCODES)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().snn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def decode_words(words: np.ndarray):
+    """Split packed synaptic words into (target, delay, code)."""
+    w = np.asarray(words, np.uint32)
+    return (w & 0x7FFFF).astype(np.int64), ((w >> 19) & 63).astype(np.int64), (w >> 25).astype(np.int64)
+
+
+def encode_words(tgt, delay, code) -> np.ndarray:
+    """Pack (target, delay, code) into synaptic words."""
+    t = np.asarray(tgt, np.uint32)
+    d = np.asarray(delay, np.uint32)
+    c = np.asarray(code, np.uint32)
+    return t | (d << 19) | (c << 25)

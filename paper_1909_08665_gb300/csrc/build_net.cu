@@ -1,0 +1,204 @@
+// build_net.cu -- on-device generation of the synaptic matrix (Sec. 2.1:
+// connections defined by probability per population pair, normal weights
+// and delays rounded to the time step; Sec. 3.1.2: the matrix is row-indexed
+// by presynaptic neuron, one word per synapse).
+//
+// Row j is the ascending list of targets i != j that pass the Bernoulli test
+// x < T[pop(i)][pop(j)], x = Philox(j, i>>2, 1, 0)[i&3].  Each synapse then
+// draws (Philox(j, i, 2, 0)) a 7-bit weight code (word 0 >> 25) and an 8-bit
+// delay stratum (word 1 >> 24) mapped through the source population's delay
+// table.  Word = target | delay << 19 | code << 25.
+//
+// Two passes over the N x N pairs (count, then fill) keep the rows exact and
+// contiguous; one CTA owns one row, 256 threads x 4 Philox lanes per tile of
+// 1024 targets, so the write order is the target order.
+#include "snn_internal.cuh"
+
+namespace snn {
+
+namespace {
+
+template <int BLOCK>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp,
+                                                    uint32_t& total) {
+    constexpr int NW = BLOCK / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NW ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t wp = warp ? s_warp[warp - 1] : 0u;
+    total = s_warp[NW - 1];
+    __syncthreads();
+    return wp + x - v;
+}
+
+// connection bits of the 4 targets 4g .. 4g+3 of row j (bit k = target 4g+k)
+__device__ __forceinline__ uint32_t conn_bits(const BuildParams& bp, const uint64_t* s_thr,
+                                              int32_t j, int32_t g) {
+    const uint4 r = philox(make_uint4((uint32_t)j, (uint32_t)g, kStreamConn, 0u), bp.key0,
+                           bp.key1);
+    uint32_t bits = 0;
+#pragma unroll
+    for (int lane = 0; lane < 4; ++lane) {
+        const int32_t i = 4 * g + lane;
+        if (i < bp.n && i != j) {
+            const int p = pop_index(bp.pop_start, bp.n_pop, i);
+            if ((uint64_t)lane_of(r, lane) < s_thr[p]) bits |= 1u << lane;
+        }
+    }
+    return bits;
+}
+
+__global__ void __launch_bounds__(kBuildThreads)
+k_build_count(const __grid_constant__ BuildParams bp, uint32_t* rowlen) {
+    __shared__ uint32_t s_warp[kBuildThreads / 32];
+    __shared__ uint64_t s_thr[kMaxPop];
+    const int32_t j = blockIdx.x;
+    const int q = pop_index(bp.pop_start, bp.n_pop, j);
+    if (threadIdx.x < kMaxPop) s_thr[threadIdx.x] = bp.conn_thr[threadIdx.x][q];
+    __syncthreads();
+    uint32_t cnt = 0;
+    const int32_t ngrp = (bp.n + 3) >> 2;
+    for (int32_t g = threadIdx.x; g < ngrp; g += kBuildThreads)
+        cnt += __popc(conn_bits(bp, s_thr, j, g));
+    uint32_t total;
+    block_excl_scan<kBuildThreads>(cnt, s_warp, total);
+    if (threadIdx.x == 0) rowlen[j] = total;
+}
+
+// exclusive scan of the row lengths into 64-bit row starts (one CTA)
+__global__ void __launch_bounds__(1024)
+k_build_scan(const uint32_t* __restrict__ rowlen, int n, unsigned long long* row_start) {
+    __shared__ uint32_t s_warp[32];
+    unsigned long long carry = 0;
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < n ? rowlen[i] : 0u;
+        uint32_t total;
+        const uint32_t off = block_excl_scan<1024>(v, s_warp, total);
+        if (i < n) row_start[i] = carry + off;
+        carry += total;
+    }
+    if (threadIdx.x == 0) row_start[n] = carry;
+}
+
+// segment offsets of row j: seg[j][c] = first word whose target >= part_lo[c]
+__device__ __forceinline__ void row_segments(const uint32_t* words, unsigned long long base,
+                                             uint32_t len, const int32_t* part_lo, int n_part,
+                                             uint32_t* seg_row) {
+    for (int c = threadIdx.x; c <= n_part; c += blockDim.x) {
+        const uint32_t lim = (uint32_t)part_lo[c];
+        uint32_t a = 0, b = len;
+        while (a < b) {
+            const uint32_t m = (a + b) >> 1;
+            if ((words[base + m] & kTgtMask) < lim) a = m + 1;
+            else b = m;
+        }
+        seg_row[c] = (uint32_t)(base + a);
+    }
+}
+
+__global__ void __launch_bounds__(kBuildThreads)
+k_build_fill(const __grid_constant__ BuildParams bp, const unsigned long long* row_start,
+             uint32_t* words, uint32_t* seg) {
+    __shared__ uint32_t s_warp[kBuildThreads / 32];
+    __shared__ uint64_t s_thr[kMaxPop];
+    __shared__ uint8_t s_dtab[kDCodes];
+    const int32_t j = blockIdx.x;
+    const int q = pop_index(bp.pop_start, bp.n_pop, j);
+    if (threadIdx.x < kMaxPop) s_thr[threadIdx.x] = bp.conn_thr[threadIdx.x][q];
+    for (int k = threadIdx.x; k < kDCodes; k += kBuildThreads) s_dtab[k] = bp.dtab[q * kDCodes + k];
+    __syncthreads();
+    const unsigned long long base = row_start[j];
+    uint32_t running = 0;
+    const int32_t ngrp = (bp.n + 3) >> 2;
+    for (int32_t g0 = 0; g0 < ngrp; g0 += kBuildThreads) {
+        const int32_t g = g0 + threadIdx.x;
+        const uint32_t bits = g < ngrp ? conn_bits(bp, s_thr, j, g) : 0u;
+        uint32_t total;
+        const uint32_t off = block_excl_scan<kBuildThreads>(__popc(bits), s_warp, total);
+        unsigned long long pos = base + running + off;
+#pragma unroll
+        for (int lane = 0; lane < 4; ++lane) {
+            if (bits & (1u << lane)) {
+                const uint32_t i = (uint32_t)(4 * g + lane);
+                const uint4 y = philox(make_uint4((uint32_t)j, i, kStreamSyn, 0u), bp.key0, bp.key1);
+                const uint32_t code = y.x >> 25;
+                const uint32_t d = s_dtab[y.y >> 24];
+                words[pos++] = i | (d << kTgtBits) | (code << 25);
+            }
+        }
+        running += total;
+    }
+    __syncthreads();
+    row_segments(words, base, running, bp.part_lo, bp.n_part,
+                 seg + (size_t)j * (size_t)(bp.n_part + 1));
+}
+
+__global__ void __launch_bounds__(kBuildThreads)
+k_seg_from_rows(const unsigned long long* row_start, const uint32_t* words,
+                const int32_t* part_lo, int n_part, uint32_t* seg) {
+    const int32_t j = blockIdx.x;
+    const unsigned long long base = row_start[j];
+    const uint32_t len = (uint32_t)(row_start[j + 1] - base);
+    row_segments(words, base, len, part_lo, n_part, seg + (size_t)j * (size_t)(n_part + 1));
+}
+
+// default initial potential: uniform on [lo, hi) from 24 random bits, fp32
+__global__ void k_init_u(int n, uint32_t k0, uint32_t k1, float lo, float hi, float* u) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 r = philox(make_uint4((uint32_t)i, 0u, kStreamInit, 0u), k0, k1);
+    const float span = __fsub_rn(hi, lo);
+    const float unit = __fmul_rn(__uint2float_rn(r.x >> 8), 5.9604644775390625e-08f);
+    u[i] = __fadd_rn(lo, __fmul_rn(span, unit));
+}
+
+}  // namespace
+
+cudaError_t launch_build_count(const BuildParams& bp, uint32_t* rowlen, cudaStream_t s) {
+    k_build_count<<<bp.n, kBuildThreads, 0, s>>>(bp, rowlen);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_scan(const uint32_t* rowlen, int n, unsigned long long* row_start,
+                              cudaStream_t s) {
+    k_build_scan<<<1, 1024, 0, s>>>(rowlen, n, row_start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_fill(const BuildParams& bp, const unsigned long long* row_start,
+                              uint32_t* words, uint32_t* seg, cudaStream_t s) {
+    k_build_fill<<<bp.n, kBuildThreads, 0, s>>>(bp, row_start, words, seg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_from_rows(const unsigned long long* row_start, const uint32_t* words,
+                                 int n, const int32_t* part_lo, int n_part, uint32_t* seg,
+                                 cudaStream_t s) {
+    k_seg_from_rows<<<n, kBuildThreads, 0, s>>>(row_start, words, part_lo, n_part, seg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(int n, uint32_t key0, uint32_t key1, float lo, float hi,
+                              float* u, cudaStream_t s) {
+    k_init_u<<<(n + 255) / 256, 256, 0, s>>>(n, key0, key1, lo, hi, u);
+    return cudaGetLastError();
+}
+
+}  // namespace snn

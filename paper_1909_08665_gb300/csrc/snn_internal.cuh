@@ -1,0 +1,162 @@
+// snn_internal.cuh -- device-side definitions shared by the kernels of the
+// GB300 microcircuit library (not part of the public ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace snn {
+
+constexpr int kMaxPop = 8;
+constexpr int kWCodes = 128;
+constexpr int kDCodes = 256;
+constexpr int kPoisTable = 32;
+constexpr int kRing = 64;                 // delay slots (delays 1..63)
+constexpr int kStepThreads = 512;         // threads per CTA of the step kernel
+constexpr int kChunk = 1024;              // spikes per delivery chunk
+constexpr int kBuildThreads = 256;        // threads per CTA of the build kernels
+constexpr uint32_t kTgtBits = 19;
+constexpr uint32_t kTgtMask = (1u << kTgtBits) - 1u;
+
+// Philox stream tags (third counter word)
+constexpr uint32_t kStreamConn = 1u;
+constexpr uint32_t kStreamSyn = 2u;
+constexpr uint32_t kStreamPois = 3u;
+constexpr uint32_t kStreamInit = 4u;
+
+// status bits
+constexpr uint32_t kStatusTimeout = 1u;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the two 32x32->64-bit
+// products with multipliers 0xD2511F53 (word 0) and 0xCD9E8D57 (word 2), the
+// word permutation (hi1^c1^k0, lo1, hi0^c3^k1, lo0) and the Weyl key bumps
+// 0x9E3779B9 / 0xBB67AE85.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t lane_of(const uint4& v, int lane) {
+    return lane == 0 ? v.x : lane == 1 ? v.y : lane == 2 ? v.z : v.w;
+}
+
+// ---------------------------------------------------------------------------
+// memory-model helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_gpu_add(uint32_t* p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// parameters
+// ---------------------------------------------------------------------------
+struct BuildParams {
+    int32_t n;                          // neurons
+    int32_t n_pop;
+    int32_t pop_start[kMaxPop + 1];
+    int32_t n_part;
+    uint32_t key0, key1;
+    uint64_t conn_thr[kMaxPop][kMaxPop];  // [target][source], compare x < thr
+    const uint8_t* dtab;                // device [8][256] delays in steps
+    const int32_t* part_lo;             // device [n_part + 1]
+};
+
+struct StepParams {
+    int32_t n, n_pop, n_part, ncmax;
+    int32_t pop_start[kMaxPop + 1];
+    float P22, P21, P11, theta;
+    float cdc[kMaxPop];                 // P20 * I_DC per population (mode 1)
+    int32_t n_ref, wext_q, mode;
+    uint32_t key0, key1;
+    int64_t t0;
+    int32_t n_steps;
+    uint32_t ras_cap;                   // raster capacity per partition
+    uint64_t timeout_ns;
+    int32_t inject_fault;               // 1: partition 0 never arrives
+    uint64_t pois[kMaxPop][kPoisTable]; // Poisson thresholds (x >= T -> +1)
+    // network (read only)
+    const int32_t* part_lo;             // [n_part + 1]
+    const uint32_t* seg;                // [n][n_part + 1] absolute word offsets
+    const uint32_t* words;
+    const int32_t* wtab;                // [8][8][128]
+    // state
+    float* u;
+    float* i_syn;
+    int32_t* refr;
+    int32_t* ring;                      // [n_part][kRing][ncmax]
+    uint32_t* spk_ids;                  // [4][n_part][ncmax]
+    uint32_t* spk_cnt;                  // [4][n_part]
+    uint32_t* ras_step;                 // [n_part][ras_cap]
+    uint32_t* ras_id;
+    uint32_t* ras_n;                    // [n_part] spikes recorded (may exceed cap)
+    unsigned long long* counters;       // [0] spikes, [1] synaptic events
+    uint32_t* barrier;                  // [4] arrival counters
+    uint32_t* status;
+    uint32_t* abort_flag;
+};
+
+struct DeliverParams {
+    int32_t n, n_pop, n_part, ncmax, n_spikes;
+    int32_t pop_start[kMaxPop + 1];
+    int64_t t;
+    const uint32_t* spikes;
+    const int32_t* part_lo;
+    const uint32_t* seg;
+    const uint32_t* words;
+    const int32_t* wtab;
+    int32_t* ring;
+    unsigned long long* counters;
+};
+
+__device__ __forceinline__ int pop_index(const int32_t* pop_start, int n_pop, int32_t i) {
+    int p = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxPop; ++k)
+        p += (k < n_pop && i >= pop_start[k]) ? 1 : 0;
+    return p;
+}
+
+// host-side launchers (defined in the .cu files)
+cudaError_t launch_build_count(const BuildParams& bp, uint32_t* rowlen, cudaStream_t s);
+cudaError_t launch_build_scan(const uint32_t* rowlen, int n, unsigned long long* row_start,
+                              cudaStream_t s);
+cudaError_t launch_build_fill(const BuildParams& bp, const unsigned long long* row_start,
+                              uint32_t* words, uint32_t* seg, cudaStream_t s);
+cudaError_t launch_seg_from_rows(const unsigned long long* row_start, const uint32_t* words,
+                                 int n, const int32_t* part_lo, int n_part, uint32_t* seg,
+                                 cudaStream_t s);
+cudaError_t launch_init_state(int n, uint32_t key0, uint32_t key1, float lo, float hi,
+                              float* u, cudaStream_t s);
+int step_kernel_variant(int npt, bool smem_ring);
+size_t step_shared_bytes(int ncmax, int n_part, bool smem_ring);
+cudaError_t step_kernel_configure(int npt, bool smem_ring, size_t smem);
+cudaError_t launch_step(const StepParams& sp, int npt, bool smem_ring, size_t smem,
+                        cudaStream_t s);
+cudaError_t launch_deliver(const DeliverParams& dp, int tiling, cudaStream_t s);
+
+}  // namespace snn

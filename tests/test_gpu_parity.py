@@ -1,0 +1,234 @@
+"""GPU path versus the CPU oracle, element by element, through the C ABI.
+
+The bar is bit-exact: spike rasters (step, id), fp32 membrane potentials and
+synaptic currents (compared as bit patterns), refractory counters, int32 ring
+buffers and the synaptic matrix itself.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+from helpers import custom_network, tiny_config
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_1909_08665_gb300 as pkg  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def cfg01():
+    return workload.microcircuit(0.1)
+
+
+@pytest.fixture(scope="module")
+def onet01(cfg01):
+    return oracle.Network(cfg01)
+
+
+def gpu_net(cfg, **kw):
+    return pkg.Microcircuit(cfg, stream=torch.cuda.current_stream(), **kw)
+
+
+def oracle_words(onet):
+    rp, tg, dl, wc = onet.export()
+    return rp.astype(np.uint64), pkg.encode_words(tg, dl, wc)
+
+
+def assert_state_equal(net, sim):
+    g_u, g_i, g_r = net.state()
+    o_u, o_i, o_r, o_ring = sim.state()
+    np.testing.assert_array_equal(g_u.view(np.uint32), o_u.view(np.uint32))
+    np.testing.assert_array_equal(g_i.view(np.uint32), o_i.view(np.uint32))
+    np.testing.assert_array_equal(g_r, o_r)
+    assert np.all(np.abs(o_ring) < 2**31)
+    np.testing.assert_array_equal(net.ring(), o_ring.astype(np.int32))
+
+
+# ---------------------------------------------------------------------------
+# network generation
+# ---------------------------------------------------------------------------
+def test_network_matches_oracle(cfg01, onet01):
+    net = gpu_net(cfg01)
+    rp, wd, wt = net.export_network()
+    orp, owd = oracle_words(onet01)
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(wd, owd)
+    np.testing.assert_array_equal(wt, oracle.tables(cfg01)["wtab"])
+    info = net.info()
+    d, f = oracle.propagators(cfg01)
+    assert info["propagators"] == [float(v) for v in f]
+    assert info["n_ref"] == 20 and info["wext_q"] == oracle.tables(cfg01)["wext_q"]
+
+
+@pytest.mark.parametrize("n_part", [2, 5, 61, 152])
+def test_network_independent_of_partitioning(cfg01, onet01, n_part):
+    net = gpu_net(cfg01, n_part=n_part)
+    assert net.info()["n_part"] == n_part
+    _, wd, _ = net.export_network()
+    np.testing.assert_array_equal(wd, oracle_words(onet01)[1])
+
+
+# ---------------------------------------------------------------------------
+# time stepping: 10 % microcircuit, 100 ms
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n_part", [0, 2, 7, 64])
+def test_raster_and_state_bit_exact(cfg01, onet01, n_part):
+    steps = 1000
+    net = gpu_net(cfg01, n_part=n_part)
+    sim = oracle.Simulation(onet01)
+    net.step(steps)
+    net.sync()
+    sim.run(steps)
+    g_st, g_id = net.read_spikes()
+    o_st, o_id = sim.raster()
+    assert o_st.size > 1000
+    np.testing.assert_array_equal(g_st, o_st)
+    np.testing.assert_array_equal(g_id, o_id)
+    assert_state_equal(net, sim)
+    gc, oc = net.counters(), sim.counters()
+    assert gc["spikes"] == oc["spikes"] and gc["events"] == oc["events"]
+    assert not oc["saturated"]
+
+
+def test_launch_boundaries_do_not_change_results(cfg01, onet01):
+    net = gpu_net(cfg01)
+    sim = oracle.Simulation(onet01)
+    for n in (1, 1, 2, 3, 5, 117, 0, 371):
+        net.step(n)
+    net.sync()
+    sim.run(500)
+    g = net.read_spikes()
+    o = sim.raster()
+    np.testing.assert_array_equal(g[0], o[0])
+    np.testing.assert_array_equal(g[1], o[1])
+    assert_state_equal(net, sim)
+
+
+def test_user_initial_state_and_dc_input(cfg01):
+    cfg = workload.dc_variant(cfg01)
+    u0 = workload.random_membrane(cfg, seed=5)
+    net = gpu_net(cfg, u0=u0)
+    onet = oracle.Network(cfg)
+    sim = oracle.Simulation(onet, u0=u0)
+    net.step(600)
+    sim.run(600)
+    g = net.read_spikes()
+    o = sim.raster()
+    assert o[0].size > 100
+    np.testing.assert_array_equal(g[0], o[0])
+    np.testing.assert_array_equal(g[1], o[1])
+    assert_state_equal(net, sim)
+
+
+@pytest.mark.parametrize("n_part", [1, 3])
+def test_other_seed_and_scale(n_part):
+    # 5 % model (3,858 neurons): n_part 1 puts them all in one CTA
+    cfg = workload.microcircuit(0.05, seed=987654321987)
+    net = gpu_net(cfg, n_part=n_part)
+    onet = oracle.Network(cfg)
+    sim = oracle.Simulation(onet)
+    net.step(400)
+    sim.run(400)
+    g = net.read_spikes()
+    o = sim.raster()
+    np.testing.assert_array_equal(g[0], o[0])
+    np.testing.assert_array_equal(g[1], o[1])
+    assert_state_equal(net, sim)
+
+
+# ---------------------------------------------------------------------------
+# hand-set networks through snn_create_from_rows
+# ---------------------------------------------------------------------------
+def test_tiny_network_from_rows():
+    n = 6
+    weights_q = [round(87.8 * 256 * 12), round(-351.2 * 256 * 3), round(87.8 * 256 * 20)]
+    synapses = [(0, 1, 0, 3), (0, 2, 2, 15), (1, 3, 2, 1), (2, 3, 1, 5), (3, 4, 0, 40),
+                (4, 5, 2, 63), (5, 0, 1, 9), (3, 5, 2, 2), (1, 0, 1, 30)]
+    cfg = tiny_config(n, input_mode=1)
+    cfg["pop_sizes"] = [1] * n
+    cfg["pop_exc"] = [1] * n
+    cfg["i_dc"] = [520.0, 480.0, 600.0, 450.0, 500.0, 390.0, 0.0, 0.0]
+    desc = custom_network(n, synapses, weights_q)
+    wt = np.zeros((8, 8, 128), np.int32)
+    wt[:, :, :3] = np.asarray(weights_q, np.int32)
+    desc["wtab"] = wt
+    u0 = np.array([14.9, 5.0, 12.0, 0.0, 10.0, 3.0], np.float32)
+    onet = oracle.Network(cfg, custom=desc)
+    sim = oracle.Simulation(onet, u0=u0)
+    rows = {"row_ptr": desc["row_ptr"].astype(np.uint64),
+            "words": pkg.encode_words(desc["tgt"], desc["delay"], desc["wcode"]), "wtab": wt}
+    net = gpu_net(cfg, u0=u0, rows=rows)
+    net.step(700)
+    sim.run(700)
+    g = net.read_spikes()
+    o = sim.raster()
+    assert o[0].size > 20
+    np.testing.assert_array_equal(g[0], o[0])
+    np.testing.assert_array_equal(g[1], o[1])
+    assert_state_equal(net, sim)
+
+
+def test_empty_network_and_zero_steps():
+    cfg = tiny_config(100, input_mode=0, nu_bg=8.0)
+    cfg["k_ext"] = [2300.0] * 8
+    net = gpu_net(cfg)
+    assert net.info()["n_synapses"] == 0
+    net.step(0)
+    net.sync()
+    assert net.counters()["step"] == 0
+    onet = oracle.Network(cfg)
+    sim = oracle.Simulation(onet)
+    net.step(300)
+    sim.run(300)
+    g = net.read_spikes()
+    o = sim.raster()
+    assert o[0].size > 0
+    np.testing.assert_array_equal(g[0], o[0])
+    np.testing.assert_array_equal(g[1], o[1])
+    assert_state_equal(net, sim)
+
+
+# ---------------------------------------------------------------------------
+# standalone delivery: both tilings against the oracle
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n_spikes", [1, 25, 93, 4000])
+@pytest.mark.parametrize("tiling", [0, 1])
+def test_deliver_matches_oracle(cfg01, onet01, n_spikes, tiling):
+    net = gpu_net(cfg01)
+    spikes = workload.random_spike_list(net.n, n_spikes, seed=n_spikes)
+    spikes = np.r_[spikes, spikes[:3]].astype(np.uint32)     # duplicates allowed
+    d = torch.from_numpy(spikes.astype(np.int32)).cuda()
+    t = 12345
+    net.deliver(d.data_ptr(), spikes.size, t, tiling)
+    net.sync()
+    ref = onet01.deliver(spikes.astype(np.int32), t)
+    np.testing.assert_array_equal(net.ring(), ref.astype(np.int32))
+
+
+# ---------------------------------------------------------------------------
+# failure path: a barrier wait that runs out of time returns an error status
+# ---------------------------------------------------------------------------
+def test_barrier_timeout_reports_error_and_context_survives(cfg01):
+    # partition 0 withholds its arrivals: every other wait runs out (50 ms)
+    net = gpu_net(cfg01, n_part=8, timeout_s=0.05, inject_fault=1)
+    net.step(50)
+    with pytest.raises(pkg.SnnError) as e:
+        net.sync()
+    assert e.value.code == pkg.SNN_ERR_TIMEOUT
+    net.close()
+    ok = gpu_net(cfg01)
+    ok.step(10)
+    ok.sync()
+
+
+def test_raster_overflow_is_reported(cfg01):
+    net = gpu_net(cfg01, raster_capacity=1)
+    net.step(400)
+    with pytest.raises(pkg.SnnError) as e:
+        net.sync()
+    assert e.value.code == pkg.SNN_ERR_OVERFLOW
