@@ -199,6 +199,62 @@ int snn_export_network(snn_net* net, uint64_t* row_ptr_host, uint32_t* words_hos
 int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int64_t t,
                 int32_t tiling);
 
+/*
+ * snn_step_noalloc -- advance a network held entirely in caller-owned device
+ * memory by n_steps, allocating nothing.  The paper has no counterpart; it
+ * exists for callers that may not allocate device memory while they run: an
+ * application that steps the network in a closed real-time loop and has
+ * reserved all of its device memory up front cannot call cudaMalloc or
+ * cudaFree (they may synchronise the device and take unbounded time).
+ *
+ * The kernel's scratch (two spike lists and the barrier words) is a static
+ * device array of 64 + 2 * SNN_NOALLOC_MAX_NEURONS 32-bit words (about 1 MiB)
+ * that every GPU loading this library holds until the process exits.
+ * Networks above SNN_NOALLOC_MAX_NEURONS neurons are rejected with
+ * SNN_ERR_INVALID.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the one array and
+ * clears the words that must start at zero, so calls whose kernels overlap
+ * on the GPU (on different streams, or from several threads) race and give
+ * wrong results: serialise them.
+ *
+ *   cfg, seed  model parameters and Philox key, as for snn_create; the
+ *              network's row_ptr / words / wtab must be the ones exported
+ *              by snn_export_network for the same cfg (any rows in that
+ *              format are accepted).
+ *   io         device pointers, all required:
+ *                row_ptr[n+1] (uint64), words[nnz], wtab[8*8*128]   input
+ *                u[n], i_syn[n], refr[n], ring[64*n] slot-major     in/out
+ *                ras_step[ras_cap], ras_id[ras_cap]                 output
+ *                ras_n: spikes recorded; the kernel appends at *ras_n
+ *                  and counts past ras_cap (caller zeroes it)     in/out
+ *                counters[2]: spikes and synaptic events, added to  in/out
+ *                status: ORed with 1 if a grid-barrier wait gave up in/out
+ *   t0         index of the first step (it selects the ring slots and the
+ *              background draws, so consecutive calls continue a run).
+ * Asynchronous on `stream`.  Results equal snn_step on the same network.
+ */
+#define SNN_NOALLOC_MAX_NEURONS 131072
+
+typedef struct snn_noalloc_io {
+    const uint64_t* row_ptr;
+    const uint32_t* words;
+    const int32_t* wtab;
+    float* u;
+    float* i_syn;
+    int32_t* refr;
+    int32_t* ring;
+    uint32_t* ras_step;
+    uint32_t* ras_id;
+    uint32_t* ras_n;
+    int64_t ras_cap;
+    unsigned long long* counters;
+    uint32_t* status;
+} snn_noalloc_io;
+
+int snn_step_noalloc(const snn_config* cfg, uint64_t seed, const snn_noalloc_io* io,
+                     int64_t t0, int64_t n_steps, void* stream);
+
 /* snn_destroy -- free all device memory of the network (synchronises). */
 int snn_destroy(snn_net* net);
 

@@ -77,9 +77,21 @@ class SnnInfo(C.Structure):
                 ("shared_bytes", C.c_int32)]
 
 
+class SnnNoallocIO(C.Structure):
+    """Device pointers of ``snn_step_noalloc`` (all caller-owned)."""
+    _fields_ = [("row_ptr", C.c_void_p), ("words", C.c_void_p), ("wtab", C.c_void_p),
+                ("u", C.c_void_p), ("i_syn", C.c_void_p), ("refr", C.c_void_p),
+                ("ring", C.c_void_p), ("ras_step", C.c_void_p), ("ras_id", C.c_void_p),
+                ("ras_n", C.c_void_p), ("ras_cap", C.c_int64), ("counters", C.c_void_p),
+                ("status", C.c_void_p)]
+
+
+NOALLOC_MAX_NEURONS = 131072
+
 EXPORTED = ["snn_create", "snn_create_from_rows", "snn_step", "snn_sync", "snn_read_spikes",
             "snn_raster_size", "snn_read_state", "snn_read_ring", "snn_counters", "snn_get_info",
-            "snn_export_network", "snn_deliver", "snn_destroy", "snn_last_error"]
+            "snn_export_network", "snn_deliver", "snn_step_noalloc", "snn_destroy",
+            "snn_last_error"]
 
 _lib = None
 
@@ -108,6 +120,8 @@ def lib():
         L.snn_get_info.argtypes = [vp, P(SnnInfo)]
         L.snn_export_network.argtypes = [vp, P(C.c_uint64), P(C.c_uint32), P(C.c_int32)]
         L.snn_deliver.argtypes = [vp, vp, C.c_int32, C.c_int64, C.c_int32]
+        L.snn_step_noalloc.argtypes = [P(SnnConfig), C.c_uint64, P(SnnNoallocIO), C.c_int64,
+                                       C.c_int64, vp]
         L.snn_destroy.argtypes = [vp]
         L.snn_last_error.restype = C.c_char_p
         for name in EXPORTED:
@@ -277,6 +291,14 @@ class Microcircuit:
             self.close()
         except Exception:
             pass
+
+
+def step_noalloc(cfg: dict, seed: int, io: SnnNoallocIO, t0: int, n_steps: int, stream=None):
+    """``snn_step_noalloc``: step a network held in caller-owned device memory
+    (``io`` holds the device pointers); allocates no device memory."""
+    c = make_config(cfg)
+    _check(lib().snn_step_noalloc(C.byref(c), int(seed), C.byref(io), int(t0), int(n_steps),
+                                  _stream_handle(stream)))
 
 
 def decode_words(words: np.ndarray):

@@ -442,6 +442,31 @@ int check_status(snn_net* net) {
 
 }  // namespace
 
+namespace snn {
+
+// Validated model constants of a configuration (host only, no allocation).
+int host_step_constants(const snn_config* cfg, float prop[4], float cdc[kMaxPop],
+                        uint64_t pois[kMaxPop][kPoisTable], int32_t* wext_q, int32_t* n_ref) {
+    CALL(validate(cfg));
+    static thread_local snn_net tmp;   // table workspace reused by this thread
+    tmp.cfg = *cfg;
+    CALL(make_tables(&tmp));
+    for (int k = 0; k < 4; ++k) prop[k] = tmp.prop[k];
+    for (int p = 0; p < kMaxPop; ++p) {
+        cdc[p] = tmp.cdc[p];
+        for (int m = 0; m < kPoisTable; ++m) pois[p][m] = tmp.pois[p][m];
+    }
+    *wext_q = tmp.wext_q;
+    *n_ref = tmp.n_ref;
+    return SNN_OK;
+}
+
+int set_error(int code, const char* msg) { return fail(code, msg); }
+
+int set_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+}  // namespace snn
+
 extern "C" {
 
 const char* snn_last_error(void) { return g_err.c_str(); }
