@@ -187,7 +187,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     cfg = workload.microcircuit(args.scale, seed=12345 + rank)
-    chunk = STEPS_PER_BENCH_STEP
+    chunk = args.chunk
     t_build = time.time()
     net = pkg.Microcircuit(cfg, stream=stream)
     build_s = time.time() - t_build
@@ -305,6 +305,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--chunk", type=int, default=STEPS_PER_BENCH_STEP,
+                    help="time steps per bench step (profiling uses short launches)")
     ap.add_argument("--cpu-skip", type=int, default=500)
     ap.add_argument("--cpu-steps", type=int, default=4000)
     ap.add_argument("--ref-chunk", type=int, default=200)

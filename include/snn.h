@@ -106,6 +106,7 @@ typedef struct snn_info {
     float propagators[4];     /* P22, P21, P11, P20 as used (fp32) */
     int32_t wext_q;           /* background weight, 1/256 pA */
     int32_t shared_bytes;     /* dynamic shared memory of the step kernel */
+    int32_t slot_entries;     /* 8-byte entries per (row, partition) slot */
 } snn_info;
 
 typedef struct snn_net snn_net;

@@ -74,7 +74,7 @@ class SnnInfo(C.Structure):
                 ("threads", C.c_int32), ("neurons_per_thread", C.c_int32),
                 ("ring_in_shared", C.c_int32), ("max_part_neurons", C.c_int32),
                 ("n_ref", C.c_int32), ("propagators", C.c_float * 4), ("wext_q", C.c_int32),
-                ("shared_bytes", C.c_int32)]
+                ("shared_bytes", C.c_int32), ("slot_entries", C.c_int32)]
 
 
 class SnnNoallocIO(C.Structure):

@@ -61,13 +61,15 @@ struct snn_net {
     float* d_i = nullptr;
     int32_t* d_r = nullptr;
     int32_t* d_ring = nullptr;
-    uint32_t* d_spk_ids = nullptr;
-    uint32_t* d_spk_cnt = nullptr;
+    int2* d_slots = nullptr;               // [P][n][slot_entries] (weight, ring offset)
+    int32_t slot_entries = 0;
+    unsigned long long* d_msg = nullptr;   // [4][P][msg_stride] tagged spike messages
+    int32_t msg_stride = 0;
     uint32_t* d_ras_step = nullptr;
     uint32_t* d_ras_id = nullptr;
     uint32_t* d_ras_n = nullptr;
     unsigned long long* d_counters = nullptr;
-    uint32_t* d_sync = nullptr;   // [0..3] barrier, [4] status, [5] abort
+    uint32_t* d_sync = nullptr;   // [4] status, [5] abort
 };
 
 namespace {
@@ -224,8 +226,8 @@ int make_tables(snn_net* net) {
 void free_net(snn_net* net) {
     if (!net) return;
     void* ptrs[] = {net->d_part_lo, net->d_row_start, net->d_seg, net->d_words, net->d_wtab,
-                    net->d_dtab, net->d_u, net->d_i, net->d_r, net->d_ring, net->d_spk_ids,
-                    net->d_spk_cnt, net->d_ras_step, net->d_ras_id, net->d_ras_n,
+                    net->d_dtab, net->d_u, net->d_i, net->d_r, net->d_ring, net->d_msg, net->d_slots,
+                    net->d_ras_step, net->d_ras_id, net->d_ras_n,
                     net->d_counters, net->d_sync};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -299,8 +301,8 @@ int alloc_state(snn_net* net, const float* u0_host) {
     CALL(dalloc(&net->d_i, n, "I"));
     CALL(dalloc(&net->d_r, n, "refractory"));
     CALL(dalloc(&net->d_ring, (size_t)P * kRing * net->ncmax, "ring"));
-    CALL(dalloc(&net->d_spk_ids, (size_t)4 * P * net->ncmax, "spike lists"));
-    CALL(dalloc(&net->d_spk_cnt, (size_t)4 * P, "spike counts"));
+    net->msg_stride = (net->ncmax + 1 + 3) / 4 * 4;
+    CALL(dalloc(&net->d_msg, (size_t)4 * P * net->msg_stride, "spike messages"));
     CALL(dalloc(&net->d_ras_step, (size_t)P * net->ras_cap, "raster"));
     CALL(dalloc(&net->d_ras_id, (size_t)P * net->ras_cap, "raster"));
     CALL(dalloc(&net->d_ras_n, P, "raster counts"));
@@ -310,7 +312,7 @@ int alloc_state(snn_net* net, const float* u0_host) {
     CK(cudaMemsetAsync(net->d_i, 0, sizeof(float) * n, s));
     CK(cudaMemsetAsync(net->d_r, 0, sizeof(int32_t) * n, s));
     CK(cudaMemsetAsync(net->d_ring, 0, sizeof(int32_t) * (size_t)P * kRing * net->ncmax, s));
-    CK(cudaMemsetAsync(net->d_spk_cnt, 0, sizeof(uint32_t) * 4 * P, s));
+    CK(cudaMemsetAsync(net->d_msg, 0, sizeof(unsigned long long) * 4 * P * net->msg_stride, s));
     CK(cudaMemsetAsync(net->d_ras_n, 0, sizeof(uint32_t) * P, s));
     CK(cudaMemsetAsync(net->d_counters, 0, sizeof(unsigned long long) * 2, s));
     CK(cudaMemsetAsync(net->d_sync, 0, sizeof(uint32_t) * 8, s));
@@ -349,10 +351,26 @@ int common_setup(const snn_config* cfg, uint64_t seed, const snn_options* opt, v
     return SNN_OK;
 }
 
+// weight table upload and the partition slots of the step kernel
 int finish_network(snn_net* net) {
     cudaStream_t s = net->stream;
     CALL(dalloc(&net->d_wtab, kMaxPop * kMaxPop * kWCodes, "wtab"));
     CK(cudaMemcpyAsync(net->d_wtab, net->wtab, sizeof(net->wtab), cudaMemcpyHostToDevice, s));
+    uint32_t* d_max = nullptr;
+    CALL(dalloc(&d_max, 1, "segment maximum"));
+    uint32_t lmax = 0;
+    cudaError_t e = launch_max_segment(net->d_seg, net->n, net->P, d_max, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&lmax, d_max, sizeof(lmax), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_max);
+    if (e != cudaSuccess) return cuda_fail(e, "segment maximum");
+    int se = 32;
+    while (se < (int)lmax + 1) se *= 2;
+    net->slot_entries = se;
+    // + 2 entries of tail padding, like every array a bulk prefetch covers
+    CALL(dalloc(&net->d_slots, (size_t)net->n * net->P * se + 2, "partition slots"));
+    CK(launch_build_slots(net->d_words, net->d_seg, net->d_part_lo, net->d_wtab, net->n, net->P,
+                          net->n_pop, net->pop_start, net->ncmax, se, net->d_slots, s));
     CK(cudaStreamSynchronize(s));
     return SNN_OK;
 }
@@ -390,8 +408,9 @@ int build_generated(snn_net* net) {
     if (e != cudaSuccess) return cuda_fail(e, "network row count");
     if (total >= 0xffffffffull) return fail(SNN_ERR_INVALID, "more than 2^32-1 synapses");
     net->nnz = total;
-    CALL(dalloc(&net->d_words, total, "synaptic words"));
-    CALL(dalloc(&net->d_seg, (size_t)n * (P + 1), "row segments"));
+    // + 4 words: bulk L2 prefetches of a row round its end up to 16 B
+    CALL(dalloc(&net->d_words, total + 4, "synaptic words"));
+    CALL(dalloc(&net->d_seg, (size_t)n * (P + 1) + 4, "row segments"));
     CK(launch_build_fill(bp, net->d_row_start, net->d_words, net->d_seg, s));
     CK(cudaStreamSynchronize(s));
     return finish_network(net);
@@ -421,8 +440,9 @@ int build_from_rows(snn_net* net, const uint64_t* row_ptr, const uint32_t* words
     std::memcpy(net->wtab, wtab, sizeof(net->wtab));
     CALL(dalloc(&net->d_part_lo, P + 1, "partitions"));
     CALL(dalloc(&net->d_row_start, (size_t)n + 1, "row starts"));
-    CALL(dalloc(&net->d_words, total, "synaptic words"));
-    CALL(dalloc(&net->d_seg, (size_t)n * (P + 1), "row segments"));
+    // + 4 words: bulk L2 prefetches of a row round its end up to 16 B
+    CALL(dalloc(&net->d_words, total + 4, "synaptic words"));
+    CALL(dalloc(&net->d_seg, (size_t)n * (P + 1) + 4, "row segments"));
     CK(cudaMemcpyAsync(net->d_part_lo, net->part_lo.data(), sizeof(int32_t) * (P + 1),
                        cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(net->d_row_start, row_ptr, sizeof(uint64_t) * (n + 1), cudaMemcpyHostToDevice, s));
@@ -530,7 +550,10 @@ int snn_step(snn_net* net, int64_t n_steps) {
     sp.timeout_ns = net->timeout_ns;
     sp.inject_fault = net->inject_fault;
     for (int p = 0; p < kMaxPop; ++p)
-        for (int m = 0; m < kPoisTable; ++m) sp.pois[p][m] = net->pois[p][m];
+        for (int m = 0; m < kPoisTable; ++m)   // T >= 1 (validation bounds lambda)
+            sp.pois_m1[p][m] = (uint32_t)(net->pois[p][m] - 1u);
+    sp.slots = net->d_slots;
+    sp.slot_entries = net->slot_entries;
     sp.part_lo = net->d_part_lo;
     sp.seg = net->d_seg;
     sp.words = net->d_words;
@@ -539,13 +562,13 @@ int snn_step(snn_net* net, int64_t n_steps) {
     sp.i_syn = net->d_i;
     sp.refr = net->d_r;
     sp.ring = net->d_ring;
-    sp.spk_ids = net->d_spk_ids;
-    sp.spk_cnt = net->d_spk_cnt;
+    sp.row_start = net->d_row_start;
+    sp.msg = net->d_msg;
+    sp.msg_stride = net->msg_stride;
     sp.ras_step = net->d_ras_step;
     sp.ras_id = net->d_ras_id;
     sp.ras_n = net->d_ras_n;
     sp.counters = net->d_counters;
-    sp.barrier = net->d_sync;
     sp.status = net->d_sync + 4;
     sp.abort_flag = net->d_sync + 5;
     int64_t left = n_steps;
@@ -553,7 +576,6 @@ int snn_step(snn_net* net, int64_t n_steps) {
         const int64_t chunk = std::min(left, kMaxLaunch);
         sp.t0 = net->step;
         sp.n_steps = (int32_t)chunk;
-        CK(cudaMemsetAsync(net->d_sync, 0, sizeof(uint32_t) * 4, net->stream));
         CK(cudaMemsetAsync(net->d_sync + 5, 0, sizeof(uint32_t), net->stream));
         CK(launch_step(sp, net->npt, net->smem_ring, net->smem, net->stream));
         net->step += chunk;
@@ -660,6 +682,7 @@ int snn_get_info(snn_net* net, snn_info* info) {
     for (int k = 0; k < 4; ++k) info->propagators[k] = net->prop[k];
     info->wext_q = net->wext_q;
     info->shared_bytes = (int32_t)net->smem;
+    info->slot_entries = net->slot_entries;
     return SNN_OK;
 }
 

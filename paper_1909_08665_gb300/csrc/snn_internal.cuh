@@ -86,6 +86,10 @@ struct BuildParams {
     const int32_t* part_lo;             // device [n_part + 1]
 };
 
+struct SlotPops {
+    int32_t pop_start[kMaxPop + 1];
+};
+
 struct StepParams {
     int32_t n, n_pop, n_part, ncmax;
     int32_t pop_start[kMaxPop + 1];
@@ -97,25 +101,27 @@ struct StepParams {
     int32_t n_steps;
     uint32_t ras_cap;                   // raster capacity per partition
     uint64_t timeout_ns;
-    int32_t inject_fault;               // 1: partition 0 never arrives
-    uint64_t pois[kMaxPop][kPoisTable]; // Poisson thresholds (x >= T -> +1)
+    int32_t inject_fault;               // 1: partition 0 never publishes
+    int32_t msg_stride;                 // 64-bit words per message (>= ncmax + 1)
+    int32_t slot_entries;               // 8-byte entries per partition slot (power of 2, >= 32)
+    uint32_t pois_m1[kMaxPop][kPoisTable];  // Poisson thresholds minus 1 (x > T-1 -> +1)
     // network (read only)
     const int32_t* part_lo;             // [n_part + 1]
     const uint32_t* seg;                // [n][n_part + 1] absolute word offsets
     const uint32_t* words;
     const int32_t* wtab;                // [8][8][128]
+    const unsigned long long* row_start;  // [n + 1] row offsets
+    const int2* slots;                  // [n_part][n][slot_entries] (weight, ring offset)
     // state
     float* u;
     float* i_syn;
     int32_t* refr;
     int32_t* ring;                      // [n_part][kRing][ncmax]
-    uint32_t* spk_ids;                  // [4][n_part][ncmax]
-    uint32_t* spk_cnt;                  // [4][n_part]
+    unsigned long long* msg;            // [4][n_part][msg_stride] tagged spike messages
     uint32_t* ras_step;                 // [n_part][ras_cap]
     uint32_t* ras_id;
     uint32_t* ras_n;                    // [n_part] spikes recorded (may exceed cap)
     unsigned long long* counters;       // [0] spikes, [1] synaptic events
-    uint32_t* barrier;                  // [4] arrival counters
     uint32_t* status;
     uint32_t* abort_flag;
 };
@@ -150,6 +156,12 @@ cudaError_t launch_build_fill(const BuildParams& bp, const unsigned long long* r
 cudaError_t launch_seg_from_rows(const unsigned long long* row_start, const uint32_t* words,
                                  int n, const int32_t* part_lo, int n_part, uint32_t* seg,
                                  cudaStream_t s);
+cudaError_t launch_max_segment(const uint32_t* seg, int n, int n_part, uint32_t* out,
+                               cudaStream_t s);
+cudaError_t launch_build_slots(const uint32_t* words, const uint32_t* seg, const int32_t* part_lo,
+                               const int32_t* wtab, int n, int n_part, int n_pop,
+                               const int32_t* pop_start, int ncmax, int slot_entries, int2* slots,
+                               cudaStream_t s);
 cudaError_t launch_init_state(int n, uint32_t key0, uint32_t key1, float lo, float hi,
                               float* u, cudaStream_t s);
 int step_kernel_variant(int npt, bool smem_ring);

@@ -4,22 +4,35 @@
 // One persistent cooperative launch runs n steps.  CTA c owns the neuron
 // range [part_lo[c], part_lo[c+1]): their state lives in registers and their
 // 64-slot synaptic-input ring buffers live in shared memory (or in a
-// partition-private global block when they do not fit).  Every synaptic row
-// is stored with one segment per partition, so CTA c reads only the words
-// that target its own neurons and adds them with shared-memory atomics.
+// partition-private global block when they do not fit).  Besides the plain
+// rows, every row j has one fixed-size slot per partition c holding the count
+// and the synapses of j onto c as (fixed-point weight, ring offset) pairs, so
+// CTA c reads exactly its own synapses of a spike with one coalesced load, no
+// offset lookup and no table lookup, and adds them with shared-memory atomics.
+// (A producer-side L2 prefetch of the rows of emitted spikes was measured and
+// gave no gain once the slots are read in one round trip, so there is none.)
 //
 // Per step t the order is:
 //   A(t)  u_t from (u_{t-1}, I_{t-1}); threshold, reset, refractory; the
-//         spikes of step t are compacted with warp ballots into the CTA's
-//         spike list and raster; the CTA arrives at barrier slot t mod 4.
-//   wait  barrier of step t-1 (all CTAs published their spikes of t-1).
-//   D     deliver the spikes of step t-1 into ring slots t-1+d (d >= 1).
-//   C(t)  acc = ring[t], cleared; Poisson count; I_t = P11 I_{t-1} + acc/256.
+//         spikes of step t are compacted with warp ballots and published as
+//         a message of 64-bit words (tag = t+1, value) -- the count and the
+//         neuron ids -- and the rows of those neurons are prefetched to L2;
+//         the Poisson background count of step t is drawn.
+//   D     wait for every partition's message of step t-1 (each word carries
+//         its own tag, so a matching tag is both the grid-wide barrier and
+//         the data; no fence, no counter) and deliver those spikes into ring
+//         slots t-1+d (d >= 1): per warp, batches of 4 spikes whose segment
+//         bounds and words are all loaded before the shared-memory atomics.
+//   C(t)  acc = ring[t] (cleared) + background; I_t = P11 I_{t-1} + acc/256.
 // A(t+1) needs only I_t, and the spikes of step t reach no input before
 // slot t+1, so the spike exchange of one step overlaps the next step's
-// membrane update: one grid-wide wait per step, whose latency is hidden
-// behind A.  All results equal the sequential order of the method (integer
-// accumulation, fp32 operations in a fixed order, no FMA contraction).
+// membrane update.  All results equal the sequential order of the method
+// (integer accumulation, fp32 operations in a fixed order, no FMA).
+//
+// Message slots rotate over 4 steps.  A partition can run at most one step
+// ahead of the slowest (it waits for everyone's step t-1 message before it
+// publishes step t+1), so a slot is never rewritten while it is being read.
+// Tags are 32-bit: runs are limited to 2^32 - 2 steps (about 119 h).
 #include "snn_internal.cuh"
 
 namespace snn {
@@ -31,7 +44,7 @@ constexpr uint32_t kStatusRasterOverflow = 2u;
 // shared-memory layout (bytes), identical on host and device
 // ---------------------------------------------------------------------------
 struct SmemLayout {
-    uint32_t wtab, pois, warp, misc, cntoff, st, wo, q, pop, ring, total;
+    uint32_t pois, warp, misc, cntoff, inl, spk, ring, total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -39,15 +52,12 @@ __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x
 __host__ __device__ inline SmemLayout smem_layout(int ncmax, int n_part, bool smem_ring) {
     SmemLayout L;
     uint32_t o = 0;
-    L.wtab = o;   o += kMaxPop * kMaxPop * kWCodes * 4;
-    L.pois = o;   o += kMaxPop * kPoisTable * 8;
+    L.pois = o;   o += kMaxPop * kPoisTable * 4;
     L.warp = o;   o += 32 * 4;
     L.misc = o;   o += 32 * 4;
     L.cntoff = o; o = align_up(o + (uint32_t)(n_part + 1) * 4, 16);
-    L.st = o;     o += kChunk * 4;
-    L.wo = o;     o = align_up(o + (kChunk + 1) * 4, 16);
-    L.q = o;      o = align_up(o + kChunk, 16);
-    L.pop = o;    o = align_up(o + (uint32_t)ncmax, 16);
+    L.inl = o;    o += (uint32_t)n_part * 3 * 8;
+    L.spk = o;    o += kChunk * 4;
     L.ring = o;
     if (smem_ring) o += (uint32_t)kRing * (uint32_t)ncmax * 4;
     L.total = o;
@@ -94,13 +104,16 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t (&v)[ITEMS], uint32_t* s
     return total;
 }
 
-// bounded wait until *ctr >= target (thread 0 only); false on timeout/abort
-__device__ bool wait_geq(const StepParams& sp, const uint32_t* ctr, uint32_t target) {
-    const uint64_t t_start = globaltimer_ns();
+__device__ __forceinline__ uint32_t tag_of(unsigned long long w) { return (uint32_t)(w >> 32); }
+
+// bounded-time poll of one message word until it carries `tag`
+__device__ bool poll_word(const StepParams& sp, const unsigned long long* p, uint32_t tag,
+                          unsigned long long& w) {
+    uint64_t t_start = 0;
     uint32_t iter = 0;
-    while (true) {
-        if (ld_acquire_gpu(ctr) >= target) return true;
-        if ((++iter & 255u) == 0u) {
+    while (tag_of(w) != tag) {
+        if (iter == 0) t_start = globaltimer_ns();
+        if ((++iter & 31u) == 0u) {
             if (ld_relaxed_gpu(sp.abort_flag) != 0u) return false;
             if (globaltimer_ns() - t_start > sp.timeout_ns || iter > 0x7fffffffu) {
                 atomicOr(sp.status, kStatusTimeout);
@@ -108,87 +121,150 @@ __device__ bool wait_geq(const StepParams& sp, const uint32_t* ctr, uint32_t tar
                 return false;
             }
         }
+        w = __ldcg(p);
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// the spikes s_spk[0, m) of step tb into this CTA's ring: batches of 4 spikes
+// per warp.  The slot of (spike, this partition) holds the count and the
+// synapses as (weight, ring offset) pairs; each lane loads entries lane and
+// lane+32 of all 4 slots (all loads in flight at once), then adds each weight
+// at (tb mod 64) * ncmax + offset, wrapped into the 64-slot ring.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void deliver_batches(const StepParams& sp, const uint32_t* s_spk,
+                                                uint32_t m, int c, int64_t tb, int32_t* ring,
+                                                unsigned long long& events) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t S_e = (uint32_t)sp.slot_entries;
+    const int32_t R = kRing * sp.ncmax;                  // ring words of this CTA
+    const int32_t base_t = (int32_t)(((uint32_t)tb & (kRing - 1)) * (uint32_t)sp.ncmax);
+    const size_t part_base = (size_t)c * (size_t)sp.n;
+    for (uint32_t g0 = (uint32_t)warp * 4u; g0 < m; g0 += (uint32_t)kWarps * 4u) {
+        const int2* sl[4];
+        int2 ev[4][2];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool ok = g0 + (uint32_t)k < m;
+            const uint32_t id = ok ? s_spk[g0 + k] : 0u;
+            sl[k] = sp.slots + (part_base + id) * S_e;
+            ev[k][0] = ok ? __ldg(sl[k] + lane) : make_int2(0, 0);
+            ev[k][1] = (ok && S_e > 32u) ? __ldg(sl[k] + 32 + lane) : make_int2(0, 0);
+        }
+        // entry 0 of a slot is its count; entry e >= 1 is (weight, offset)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t cnt = (uint32_t)__shfl_sync(0xffffffffu, ev[k][0].x, 0);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t e = (uint32_t)lane + 32u * (uint32_t)h;
+                if (e >= 1u && e <= cnt) {
+                    int32_t a = base_t + ev[k][h].y;
+                    a -= a >= R ? R : 0;
+                    atomicAdd(&ring[a], ev[k][h].x);
+                }
+            }
+            // slots longer than 63 entries (few partitions only)
+            for (uint32_t e = 64u + (uint32_t)lane; e <= cnt; e += 32u) {
+                const int2 x = __ldg(sl[k] + e);
+                int32_t a = base_t + x.y;
+                a -= a >= R ? R : 0;
+                atomicAdd(&ring[a], x.x);
+            }
+            if (lane == 0) events += cnt;
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
-// delivery of the spike list `list` (spikes of step tb) into this CTA's ring
+// delivery of the spikes of step tb (message tag tb+1) into this CTA's ring;
+// returns false if a wait timed out or another CTA aborted
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void deliver_list(const StepParams& sp, unsigned char* smem,
-                                             const SmemLayout& L, int c, int32_t lo, int list,
+__device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char* smem,
+                                             const SmemLayout& L, int c, int32_t lo,
                                              int64_t tb, int32_t* ring,
-                                             unsigned long long& events) {
+                                             unsigned long long& events,
+                                             const ulonglong2& pre_a, const ulonglong2& pre_b) {
     const int tid = threadIdx.x;
     const int P = sp.n_part;
-    const int32_t* s_wtab = reinterpret_cast<const int32_t*>(smem + L.wtab);
+    const int list = (int)(tb & 3);
+    const uint32_t tag = (uint32_t)(tb + 1);
+    const int lane = tid & 31, warp = tid >> 5;
     uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + L.warp);
-    uint32_t* s_cntoff = reinterpret_cast<uint32_t*>(smem + L.cntoff);
-    uint32_t* s_st = reinterpret_cast<uint32_t*>(smem + L.st);
-    uint32_t* s_wo = reinterpret_cast<uint32_t*>(smem + L.wo);
-    uint8_t* s_q = smem + L.q;
-    const uint8_t* s_pop = smem + L.pop;
+    volatile uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + L.misc);
+    unsigned long long* s_inl = reinterpret_cast<unsigned long long*>(smem + L.inl);
+    uint32_t* s_spk = reinterpret_cast<uint32_t*>(smem + L.spk);
+    const unsigned long long* msg = sp.msg + (size_t)list * P * sp.msg_stride;
 
-    // 1. spike counts of all partitions -> offsets
-    uint32_t cnt[1] = {tid < P ? __ldcg(&sp.spk_cnt[list * P + tid]) : 0u};
-    const uint32_t S = block_scan<1>(cnt, s_warp);
-    if (tid < P) s_cntoff[tid] = cnt[0];
-    if (tid == 0) s_cntoff[P] = S;
+    // 1. every partition's header word: the wait and the spike count at once;
+    //    the three words after it usually hold all of that partition's ids.
+    //    pre_a/pre_b are the first 4 words as loaded by the caller (early);
+    //    a stale header is simply polled again.
+    uint32_t cnt[1] = {0u};
+    const unsigned long long* m_mine = msg + (size_t)tid * sp.msg_stride;
+    if (tid < P) {
+        const ulonglong2 a = pre_a;
+        const ulonglong2 b = pre_b;
+        unsigned long long h = a.x;
+        if (!poll_word(sp, m_mine, tag, h)) s_misc[2] = 1u;
+        cnt[0] = (uint32_t)h;
+        s_inl[tid * 3 + 0] = a.y;
+        s_inl[tid * 3 + 1] = b.x;
+        s_inl[tid * 3 + 2] = b.y;
+    }
+    const uint32_t my_cnt = cnt[0];
+    // 2a. usual case, one barrier: each header reader appends its partition's
+    //     ids to the shared list at a position taken from a shared counter
+    if (tid < P && my_cnt > 0u) {
+        const uint32_t at = atomicAdd(const_cast<uint32_t*>(&s_misc[3]), my_cnt);
+        if (at + my_cnt <= (uint32_t)kChunk) {
+            for (uint32_t i = 0; i < my_cnt; ++i) {
+                const unsigned long long* mp = m_mine + 1 + i;
+                unsigned long long e = i < 3 ? s_inl[tid * 3 + i] : __ldcg(mp);
+                uint32_t id = 0u;                    // in range if a wait gives up
+                if (poll_word(sp, mp, tag, e)) id = (uint32_t)e;
+                else s_misc[2] = 1u;
+                s_spk[at + i] = id;
+            }
+        }
+    }
     __syncthreads();
+    const uint32_t S_fast = s_misc[3];
+    if (s_misc[2]) return false;
+    if (S_fast <= (uint32_t)kChunk) {
+        deliver_batches(sp, s_spk, S_fast, c, tb, ring, events);
+        __syncthreads();
+        if (tid == 0) s_misc[3] = 0u;
+        return s_misc[2] == 0u;
+    }
+    // 2b. more than kChunk spikes: offsets by a block-wide scan, in chunks
+    const uint32_t S = block_scan<1>(cnt, s_warp);   // cnt[0] <- my offset
+    if (tid == 0) s_misc[3] = 0u;
+    const uint32_t my_off = cnt[0];
 
     for (uint32_t base = 0; base < S; base += kChunk) {
-        const int m = (int)min((uint32_t)kChunk, S - base);
-        // 2. spike ids -> this partition's segment of each row
-        uint32_t len[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int x = tid * 2 + k;
-            len[k] = 0;
-            if (x < m) {
-                const uint32_t g = base + (uint32_t)x;
-                int a = 0, b = P;                   // s_cntoff[a] <= g < s_cntoff[b]
-                while (b - a > 1) {
-                    const int mid = (a + b) >> 1;
-                    if (s_cntoff[mid] <= g) a = mid;
-                    else b = mid;
-                }
-                const uint32_t id = __ldcg(&sp.spk_ids[((size_t)list * P + a) * sp.ncmax +
-                                                       (g - s_cntoff[a])]);
-                const uint32_t* sg = sp.seg + (size_t)id * (size_t)(P + 1) + c;
-                const uint32_t st = __ldg(sg);
-                const uint32_t en = __ldg(sg + 1);
-                s_st[x] = st;
-                s_q[x] = (uint8_t)pop_index(sp.pop_start, sp.n_pop, (int32_t)id);
-                len[k] = en - st;
+        const uint32_t m = min((uint32_t)kChunk, S - base);
+        // 2. the spike ids of this chunk into a shared list, each partition's
+        //    ids written by the thread that read its header
+        if (tid < P) {
+            // this partition's ids i with base <= my_off + i < base + m
+            const uint32_t i0 = base > my_off ? base - my_off : 0u;
+            const uint32_t i1 = base + m > my_off ? min(my_cnt, base + m - my_off) : 0u;
+            for (uint32_t i = i0; i < i1; ++i) {
+                const unsigned long long* mp = m_mine + 1 + i;
+                unsigned long long e = i < 3 ? s_inl[tid * 3 + i] : __ldcg(mp);
+                uint32_t id = 0u;                    // in range if a wait gives up
+                if (poll_word(sp, mp, tag, e)) id = (uint32_t)e;
+                else s_misc[2] = 1u;
+                s_spk[my_off + i - base] = id;
             }
         }
-        const uint32_t W = block_scan<2>(len, s_warp);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int x = tid * 2 + k;
-            if (x < m) s_wo[x] = len[k];
-        }
-        if (tid == 0) s_wo[m] = W;
         __syncthreads();
-        // 3. words of all segments, flattened over the CTA
-        for (uint32_t w = tid; w < W; w += kStepThreads) {
-            int a = 0, b = m;                       // s_wo[a] <= w < s_wo[b]
-            while (b - a > 1) {
-                const int mid = (a + b) >> 1;
-                if (s_wo[mid] <= w) a = mid;
-                else b = mid;
-            }
-            const uint32_t word = __ldg(&sp.words[s_st[a] + (w - s_wo[a])]);
-            const int32_t local = (int32_t)(word & kTgtMask) - lo;
-            const uint32_t d = (word >> kTgtBits) & 63u;
-            const uint32_t code = word >> 25;
-            const int p = s_pop[local];
-            const int32_t wt = s_wtab[(p * kMaxPop + s_q[a]) * kWCodes + code];
-            const uint32_t slot = (uint32_t)(tb + d) & (kRing - 1);
-            atomicAdd(&ring[slot * (uint32_t)sp.ncmax + (uint32_t)local], wt);
-        }
-        if (tid == 0) events += W;
+        deliver_batches(sp, s_spk, m, c, tb, ring, events);
         __syncthreads();
     }
+    return s_misc[2] == 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -203,10 +279,8 @@ k_step(const __grid_constant__ StepParams sp) {
     const int c = blockIdx.x;
     const int P = sp.n_part;
     const SmemLayout L = smem_layout(sp.ncmax, P, SMEM_RING);
-    int32_t* s_wtab = reinterpret_cast<int32_t*>(smem + L.wtab);
-    uint64_t* s_pois = reinterpret_cast<uint64_t*>(smem + L.pois);
+    uint32_t* s_pois = reinterpret_cast<uint32_t*>(smem + L.pois);
     uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + L.misc);
-    uint8_t* s_pop = smem + L.pop;
 
     const int32_t lo = sp.part_lo[c];
     const int32_t nc = sp.part_lo[c + 1] - lo;
@@ -214,22 +288,20 @@ k_step(const __grid_constant__ StepParams sp) {
                               : sp.ring + (size_t)c * kRing * (size_t)sp.ncmax;
     int32_t* ring_g = sp.ring + (size_t)c * kRing * (size_t)sp.ncmax;
 
-    for (int k = tid; k < kMaxPop * kMaxPop * kWCodes; k += kStepThreads) s_wtab[k] = sp.wtab[k];
     for (int k = tid; k < kMaxPop * kPoisTable; k += kStepThreads)
-        s_pois[k] = sp.pois[k / kPoisTable][k % kPoisTable];
-    for (int k = tid; k < nc; k += kStepThreads) s_pop[k] = (uint8_t)pop_index(sp.pop_start, sp.n_pop, lo + k);
+        s_pois[k] = sp.pois_m1[k / kPoisTable][k % kPoisTable];
     if (SMEM_RING)
         for (int k = tid; k < kRing * sp.ncmax; k += kStepThreads) ring[k] = ring_g[k];
     if (tid < 32) s_misc[tid] = 0u;
 
     float u[NPT], isyn[NPT];
-    int32_t refr[NPT];
+    int32_t refr[NPT], pacc[NPT];
     int pop[NPT];
     uint4 rnd[NPT];
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
         const int li = tid + k * kStepThreads;
-        u[k] = 0.f; isyn[k] = 0.f; refr[k] = 0; pop[k] = 0;
+        u[k] = 0.f; isyn[k] = 0.f; refr[k] = 0; pop[k] = 0; pacc[k] = 0;
         rnd[k] = make_uint4(0u, 0u, 0u, 0u);
         if (li < nc) {
             u[k] = sp.u[lo + li];
@@ -245,9 +317,18 @@ k_step(const __grid_constant__ StepParams sp) {
 
     for (int s = 0; s < sp.n_steps; ++s) {
         const int64_t t = sp.t0 + s;
-        const int list = (int)(t & 3);
+        const unsigned long long tag = (unsigned long long)(uint32_t)(t + 1) << 32;
+        unsigned long long* my_msg = sp.msg + ((size_t)(t & 3) * P + c) * sp.msg_stride;
         uint32_t* my_cnt = &s_misc[s & 1];
-        // ---- A(t): membrane, threshold, compaction ----
+        // headers of step t-1 were published one step ago: load them now so
+        // the round trip overlaps A(t)
+        ulonglong2 pre_a = make_ulonglong2(0ull, 0ull), pre_b = make_ulonglong2(0ull, 0ull);
+        if (s > 0 && tid < P) {
+            const unsigned long long* m = sp.msg + ((size_t)((t - 1) & 3) * P + tid) * sp.msg_stride;
+            pre_a = __ldcg(reinterpret_cast<const ulonglong2*>(m));
+            pre_b = __ldcg(reinterpret_cast<const ulonglong2*>(m + 2));
+        }
+        // ---- A(t): membrane, threshold, compaction, publication ----
 #pragma unroll
         for (int k = 0; k < NPT; ++k) {
             const int li = tid + k * kStepThreads;
@@ -275,13 +356,31 @@ k_step(const __grid_constant__ StepParams sp) {
                 if (spk) {
                     const uint32_t pos = wbase + (uint32_t)__popc(mask & ((1u << lane) - 1u));
                     const uint32_t id = (uint32_t)(lo + li);
-                    sp.spk_ids[((size_t)list * P + c) * sp.ncmax + pos] = id;
+                    __stcg(&my_msg[1 + pos], tag | id);
                     const uint32_t rp = ras_base + pos;
                     if (rp < sp.ras_cap) {
                         sp.ras_step[(size_t)c * sp.ras_cap + rp] = (uint32_t)t;
                         sp.ras_id[(size_t)c * sp.ras_cap + rp] = id;
                     }
                 }
+            }
+            // background count of step t (independent of the network): drawn
+            // here, added to the ring input in C(t)
+            if (sp.mode == 0 && li < nc) {
+                if ((t & 3) == 0 || s == 0)
+                    rnd[k] = philox(make_uint4((uint32_t)(lo + li), (uint32_t)(t >> 2),
+                                               kStreamPois, (uint32_t)(t >> 34)),
+                                    sp.key0, sp.key1);
+                // k = #{m : x >= T_m} = #{m : x > T_m - 1}; thresholds ascend,
+                // so the tail beyond 12 only matters when all 12 are passed
+                const uint32_t x = lane_of(rnd[k], (int)(t & 3));
+                const uint32_t* thr = s_pois + pop[k] * kPoisTable;
+                int kk = 0;
+#pragma unroll
+                for (int mm = 0; mm < 12; ++mm) kk += x > thr[mm] ? 1 : 0;
+                if (kk == 12)
+                    for (int mm = 12; mm < kPoisTable; ++mm) kk += x > thr[mm] ? 1 : 0;
+                pacc[k] = kk * sp.wext_q;
             }
         }
         __syncthreads();
@@ -291,22 +390,17 @@ k_step(const __grid_constant__ StepParams sp) {
             // past a barrier; in step 0 it is still zero from the start and is
             // left alone (no barrier separates it from step 1's adds)
             if (s > 0) s_misc[(s + 1) & 1] = 0u;
-            __stcg(&sp.spk_cnt[list * P + c], nsp);
-            __threadfence();
-            if (!(sp.inject_fault == 1 && c == 0)) red_release_gpu_add(&sp.barrier[s & 3], 1u);
+            if (!(sp.inject_fault == 1 && c == 0)) __stcg(&my_msg[0], tag | nsp);
             spikes += nsp;
             if (ras_base + nsp > sp.ras_cap) atomicOr(sp.status, kStatusRasterOverflow);
         }
         ras_base += nsp;
-        // ---- wait for step t-1 and deliver its spikes ----
+        // ---- D: spikes of step t-1 ----
         if (s > 0) {
-            if (tid == 0) {
-                const uint32_t target = (uint32_t)P * (uint32_t)((s - 1) / 4 + 1);
-                if (!wait_geq(sp, &sp.barrier[(s - 1) & 3], target)) s_misc[2] = 1u;
+            if (!deliver_list(sp, smem, L, c, lo, t - 1, ring, events, pre_a, pre_b)) {
+                aborted = true;
+                break;
             }
-            __syncthreads();
-            if (s_misc[2]) { aborted = true; break; }
-            deliver_list(sp, smem, L, c, lo, (int)((t - 1) & 3), t - 1, ring, events);
         }
         // ---- C(t): ring slot t, Poisson background, synaptic current ----
         const uint32_t slot = (uint32_t)t & (kRing - 1);
@@ -315,19 +409,8 @@ k_step(const __grid_constant__ StepParams sp) {
             const int li = tid + k * kStepThreads;
             if (li < nc) {
                 int32_t* rp = &ring[slot * (uint32_t)sp.ncmax + (uint32_t)li];
-                int32_t acc = *rp;
+                const int32_t acc = *rp + pacc[k];
                 *rp = 0;
-                if (sp.mode == 0) {
-                    if ((t & 3) == 0 || s == 0)
-                        rnd[k] = philox(make_uint4((uint32_t)(lo + li), (uint32_t)(t >> 2),
-                                                   kStreamPois, (uint32_t)(t >> 34)),
-                                        sp.key0, sp.key1);
-                    const uint32_t x = lane_of(rnd[k], (int)(t & 3));
-                    const uint64_t* thr = s_pois + pop[k] * kPoisTable;
-                    int kk = 0;
-                    while (kk < kPoisTable && (uint64_t)x >= thr[kk]) ++kk;
-                    acc += kk * sp.wext_q;
-                }
                 isyn[k] = __fadd_rn(__fmul_rn(sp.P11, isyn[k]),
                                     __fmul_rn(__int2float_rn(acc), 0.00390625f));
             }
@@ -336,16 +419,14 @@ k_step(const __grid_constant__ StepParams sp) {
 
     // ---- epilogue: deliver the spikes of the last step ----
     if (!aborted && sp.n_steps > 0) {
-        const int s = sp.n_steps;
-        if (tid == 0) {
-            const uint32_t target = (uint32_t)P * (uint32_t)((s - 1) / 4 + 1);
-            if (!wait_geq(sp, &sp.barrier[(s - 1) & 3], target)) s_misc[2] = 1u;
+        const int64_t tl = sp.t0 + sp.n_steps - 1;
+        ulonglong2 pre_a = make_ulonglong2(0ull, 0ull), pre_b = make_ulonglong2(0ull, 0ull);
+        if (tid < P) {
+            const unsigned long long* m = sp.msg + ((size_t)(tl & 3) * P + tid) * sp.msg_stride;
+            pre_a = __ldcg(reinterpret_cast<const ulonglong2*>(m));
+            pre_b = __ldcg(reinterpret_cast<const ulonglong2*>(m + 2));
         }
-        __syncthreads();
-        if (!s_misc[2]) {
-            const int64_t tl = sp.t0 + s - 1;
-            deliver_list(sp, smem, L, c, lo, (int)(tl & 3), tl, ring, events);
-        }
+        deliver_list(sp, smem, L, c, lo, tl, ring, events, pre_a, pre_b);
     }
     __syncthreads();
 #pragma unroll
@@ -362,8 +443,8 @@ k_step(const __grid_constant__ StepParams sp) {
     if (tid == 0) {
         sp.ras_n[c] = ras_base;
         atomicAdd(&sp.counters[0], spikes);
-        atomicAdd(&sp.counters[1], events);
     }
+    if (lane == 0 && events) atomicAdd(&sp.counters[1], events);   // per-warp counts
 }
 
 // ---------------------------------------------------------------------------
