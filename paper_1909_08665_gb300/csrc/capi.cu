@@ -301,7 +301,9 @@ int alloc_state(snn_net* net, const float* u0_host) {
     CALL(dalloc(&net->d_i, n, "I"));
     CALL(dalloc(&net->d_r, n, "refractory"));
     CALL(dalloc(&net->d_ring, (size_t)P * kRing * net->ncmax, "ring"));
-    net->msg_stride = (net->ncmax + 1 + 3) / 4 * 4;
+    // header + ids, read in 16-byte pairs up to entry ncmax + 1 and as a
+    // 64-byte head: a multiple of 8 entries, at least ncmax + 2
+    net->msg_stride = (net->ncmax + 2 + 7) / 8 * 8;
     CALL(dalloc(&net->d_msg, (size_t)4 * P * net->msg_stride, "spike messages"));
     CALL(dalloc(&net->d_ras_step, (size_t)P * net->ras_cap, "raster"));
     CALL(dalloc(&net->d_ras_id, (size_t)P * net->ras_cap, "raster"));

@@ -39,6 +39,7 @@ namespace snn {
 
 constexpr int kWarps = kStepThreads / 32;
 constexpr uint32_t kStatusRasterOverflow = 2u;
+constexpr int kInline = 7;        // ids read together with a message header (64 B)
 
 // ---------------------------------------------------------------------------
 // shared-memory layout (bytes), identical on host and device
@@ -56,7 +57,7 @@ __host__ __device__ inline SmemLayout smem_layout(int ncmax, int n_part, bool sm
     L.warp = o;   o += 32 * 4;
     L.misc = o;   o += 32 * 4;
     L.cntoff = o; o = align_up(o + (uint32_t)(n_part + 1) * 4, 16);
-    L.inl = o;    o += (uint32_t)n_part * 3 * 8;
+    L.inl = o;    o += (uint32_t)n_part * kInline * 8;
     L.spk = o;    o += kChunk * 4;
     L.ring = o;
     if (smem_ring) o += (uint32_t)kRing * (uint32_t)ncmax * 4;
@@ -185,47 +186,84 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
                                              const SmemLayout& L, int c, int32_t lo,
                                              int64_t tb, int32_t* ring,
                                              unsigned long long& events,
-                                             const ulonglong2& pre_a, const ulonglong2& pre_b) {
+                                             const ulonglong2 (&pre)[4]) {
     const int tid = threadIdx.x;
     const int P = sp.n_part;
     const int list = (int)(tb & 3);
     const uint32_t tag = (uint32_t)(tb + 1);
-    const int lane = tid & 31, warp = tid >> 5;
     uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + L.warp);
     volatile uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + L.misc);
     unsigned long long* s_inl = reinterpret_cast<unsigned long long*>(smem + L.inl);
     uint32_t* s_spk = reinterpret_cast<uint32_t*>(smem + L.spk);
     const unsigned long long* msg = sp.msg + (size_t)list * P * sp.msg_stride;
 
-    // 1. every partition's header word: the wait and the spike count at once;
-    //    the three words after it usually hold all of that partition's ids.
-    //    pre_a/pre_b are the first 4 words as loaded by the caller (early);
-    //    a stale header is simply polled again.
+    // 1. every partition's 64-byte message head: the header word (the wait and
+    //    the spike count at once) and the first kInline ids.  pre[] is the
+    //    head as loaded by the caller, early; a stale head is polled again.
     uint32_t cnt[1] = {0u};
     const unsigned long long* m_mine = msg + (size_t)tid * sp.msg_stride;
     if (tid < P) {
-        const ulonglong2 a = pre_a;
-        const ulonglong2 b = pre_b;
-        unsigned long long h = a.x;
-        if (!poll_word(sp, m_mine, tag, h)) s_misc[2] = 1u;
-        cnt[0] = (uint32_t)h;
-        s_inl[tid * 3 + 0] = a.y;
-        s_inl[tid * 3 + 1] = b.x;
-        s_inl[tid * 3 + 2] = b.y;
+        ulonglong2 h[4] = {pre[0], pre[1], pre[2], pre[3]};
+        if (tag_of(h[0].x) != tag) {
+            uint64_t t_start = globaltimer_ns();
+            uint32_t iter = 0;
+            do {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    h[q] = __ldcg(reinterpret_cast<const ulonglong2*>(m_mine + 2 * q));
+                if ((++iter & 31u) == 0u) {
+                    if (ld_relaxed_gpu(sp.abort_flag) != 0u ||
+                        globaltimer_ns() - t_start > sp.timeout_ns) {
+                        if (ld_relaxed_gpu(sp.abort_flag) == 0u) {
+                            atomicOr(sp.status, kStatusTimeout);
+                            atomicExch(sp.abort_flag, 1u);
+                        }
+                        s_misc[2] = 1u;
+                        break;
+                    }
+                }
+            } while (tag_of(h[0].x) != tag);
+        }
+        cnt[0] = (uint32_t)h[0].x;
+        s_inl[tid * kInline + 0] = h[0].y;
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+            s_inl[tid * kInline + 2 * q - 1] = h[q].x;
+            s_inl[tid * kInline + 2 * q] = h[q].y;
+        }
     }
     const uint32_t my_cnt = cnt[0];
     // 2a. usual case, one barrier: each header reader appends its partition's
-    //     ids to the shared list at a position taken from a shared counter
+    //     ids to the shared list at a position taken from a shared counter;
+    //     ids beyond the inline ones are loaded 8 at a time, all in flight
     if (tid < P && my_cnt > 0u) {
         const uint32_t at = atomicAdd(const_cast<uint32_t*>(&s_misc[3]), my_cnt);
         if (at + my_cnt <= (uint32_t)kChunk) {
-            for (uint32_t i = 0; i < my_cnt; ++i) {
-                const unsigned long long* mp = m_mine + 1 + i;
-                unsigned long long e = i < 3 ? s_inl[tid * 3 + i] : __ldcg(mp);
+            for (uint32_t i = 0; i < my_cnt && i < (uint32_t)kInline; ++i) {
+                unsigned long long e = s_inl[tid * kInline + i];
                 uint32_t id = 0u;                    // in range if a wait gives up
-                if (poll_word(sp, mp, tag, e)) id = (uint32_t)e;
+                if (poll_word(sp, m_mine + 1 + i, tag, e)) id = (uint32_t)e;
                 else s_misc[2] = 1u;
                 s_spk[at + i] = id;
+            }
+            for (uint32_t i = kInline; i < my_cnt; i += 8) {
+                ulonglong2 v[4];                     // entries 1+i.. are 16-B aligned
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    v[q] = i + 2 * q < my_cnt
+                               ? __ldcg(reinterpret_cast<const ulonglong2*>(m_mine + 1 + i + 2 * q))
+                               : make_ulonglong2(0ull, 0ull);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t k = i + (uint32_t)q;
+                    if (k < my_cnt) {
+                        unsigned long long e = (q & 1) ? v[q >> 1].y : v[q >> 1].x;
+                        uint32_t id = 0u;
+                        if (poll_word(sp, m_mine + 1 + k, tag, e)) id = (uint32_t)e;
+                        else s_misc[2] = 1u;
+                        s_spk[at + k] = id;
+                    }
+                }
             }
         }
     }
@@ -253,7 +291,7 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
             const uint32_t i1 = base + m > my_off ? min(my_cnt, base + m - my_off) : 0u;
             for (uint32_t i = i0; i < i1; ++i) {
                 const unsigned long long* mp = m_mine + 1 + i;
-                unsigned long long e = i < 3 ? s_inl[tid * 3 + i] : __ldcg(mp);
+                unsigned long long e = i < (uint32_t)kInline ? s_inl[tid * kInline + i] : __ldcg(mp);
                 uint32_t id = 0u;                    // in range if a wait gives up
                 if (poll_word(sp, mp, tag, e)) id = (uint32_t)e;
                 else s_misc[2] = 1u;
@@ -322,11 +360,13 @@ k_step(const __grid_constant__ StepParams sp) {
         uint32_t* my_cnt = &s_misc[s & 1];
         // headers of step t-1 were published one step ago: load them now so
         // the round trip overlaps A(t)
-        ulonglong2 pre_a = make_ulonglong2(0ull, 0ull), pre_b = make_ulonglong2(0ull, 0ull);
+        ulonglong2 pre[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pre[q] = make_ulonglong2(0ull, 0ull);
         if (s > 0 && tid < P) {
             const unsigned long long* m = sp.msg + ((size_t)((t - 1) & 3) * P + tid) * sp.msg_stride;
-            pre_a = __ldcg(reinterpret_cast<const ulonglong2*>(m));
-            pre_b = __ldcg(reinterpret_cast<const ulonglong2*>(m + 2));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pre[q] = __ldcg(reinterpret_cast<const ulonglong2*>(m + 2 * q));
         }
         // ---- A(t): membrane, threshold, compaction, publication ----
 #pragma unroll
@@ -397,7 +437,7 @@ k_step(const __grid_constant__ StepParams sp) {
         ras_base += nsp;
         // ---- D: spikes of step t-1 ----
         if (s > 0) {
-            if (!deliver_list(sp, smem, L, c, lo, t - 1, ring, events, pre_a, pre_b)) {
+            if (!deliver_list(sp, smem, L, c, lo, t - 1, ring, events, pre)) {
                 aborted = true;
                 break;
             }
@@ -420,13 +460,15 @@ k_step(const __grid_constant__ StepParams sp) {
     // ---- epilogue: deliver the spikes of the last step ----
     if (!aborted && sp.n_steps > 0) {
         const int64_t tl = sp.t0 + sp.n_steps - 1;
-        ulonglong2 pre_a = make_ulonglong2(0ull, 0ull), pre_b = make_ulonglong2(0ull, 0ull);
+        ulonglong2 pre[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pre[q] = make_ulonglong2(0ull, 0ull);
         if (tid < P) {
             const unsigned long long* m = sp.msg + ((size_t)(tl & 3) * P + tid) * sp.msg_stride;
-            pre_a = __ldcg(reinterpret_cast<const ulonglong2*>(m));
-            pre_b = __ldcg(reinterpret_cast<const ulonglong2*>(m + 2));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pre[q] = __ldcg(reinterpret_cast<const ulonglong2*>(m + 2 * q));
         }
-        deliver_list(sp, smem, L, c, lo, tl, ring, events, pre_a, pre_b);
+        deliver_list(sp, smem, L, c, lo, tl, ring, events, pre);
     }
     __syncthreads();
 #pragma unroll
