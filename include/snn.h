@@ -256,6 +256,93 @@ typedef struct snn_noalloc_io {
 int snn_step_noalloc(const snn_config* cfg, uint64_t seed, const snn_noalloc_io* io,
                      int64_t t0, int64_t n_steps, void* stream);
 
+/*
+ * ---------------------------------------------------------------------------
+ * Batched instances.  The paper simulates one network at a time; a batch runs
+ * many independent networks of the same model (Sec. 2.1, Eq. 1) -- each with
+ * its own configuration (e.g. its own scale) and seed -- in ONE persistent
+ * cooperative kernel.  Neurons of all instances are concatenated; every step
+ * is a neuron pass over all of them, a grid barrier, delivery of every spike
+ * of the step through its own instance's rows, and a second barrier.  Every
+ * instance's raster, state and counters equal those of snn_create/snn_step
+ * with the same configuration and seed (default initial state), bit for bit.
+ *
+ * Delivery tiling per instance: at creation an autotuner times, on each
+ * instance's own rows and a spike list of the size its activity gives (about
+ * 5 Hz x N x 0.1 ms), one warp per spike (tiling 0) against one CTA per row
+ * (tiling 1), and keeps the faster; snn_batch_get_info reports both times.
+ *
+ * Steps are issued as replays of one captured CUDA graph of 1000 steps; the
+ * kernel reads its first step index from device memory and advances it, so
+ * replays need no parameter update.  Remainders (n_steps mod 1000) use a
+ * plain launch.
+ * ---------------------------------------------------------------------------
+ */
+typedef struct snn_batch snn_batch;
+
+typedef struct snn_batch_info {
+    int32_t n_instances;
+    int32_t n_neurons_total;     /* concatenated neurons of all instances */
+    int32_t n_neurons;           /* of the queried instance */
+    int64_t n_synapses;          /* of the queried instance */
+    int32_t tiling;              /* 0 warp per spike, 1 CTA per row */
+    float tune_us_warp;          /* autotuner probe times, microseconds */
+    float tune_us_block;
+    int32_t blocks, threads, neurons_per_thread;
+    int32_t graph;               /* 1 if the graph was captured */
+    int32_t graph_steps;         /* steps per graph replay */
+} snn_batch_info;
+
+/*
+ * snn_batch_create -- build n_inst networks and the batch launch.
+ *   cfgs[n_inst], seeds[n_inst]   host arrays, read during the call
+ *   opt                           may be NULL; raster_capacity is the total
+ *                                 raster capacity of the batch (default
+ *                                 64 Mi spikes), timeout_s the barrier limit,
+ *                                 inject_fault = 1 makes CTA 0 skip its
+ *                                 barrier arrivals (tests the bounded wait:
+ *                                 snn_batch_sync then reports
+ *                                 SNN_ERR_TIMEOUT); n_part is ignored
+ *   stream                        cudaStream_t of all the batch's work
+ * Errors: SNN_ERR_INVALID (n_inst outside 1..1024, bad configuration),
+ * SNN_ERR_OOM, SNN_ERR_UNSUPPORTED (not sm_103, or too many neurons for one
+ * co-resident grid).
+ */
+int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_inst,
+                     const snn_options* opt, void* stream, snn_batch** out);
+
+/* snn_batch_step -- advance every instance by n_steps (async on the stream). */
+int snn_batch_step(snn_batch* b, int64_t n_steps);
+
+/* snn_batch_sync -- wait; SNN_ERR_TIMEOUT if a barrier wait gave up,
+ * SNN_ERR_OVERFLOW if the batch raster ran out of capacity. */
+int snn_batch_sync(snn_batch* b);
+
+/* snn_batch_read_spikes -- drain the spikes of instance k recorded since the
+ * last read of that instance: (step, local neuron id) in device order (not
+ * sorted).  Synchronises.  n receives the number written (<= cap). */
+int snn_batch_read_spikes(snn_batch* b, int32_t k, uint32_t* steps_host, uint32_t* ids_host,
+                          int64_t cap, int64_t* n);
+
+/* snn_batch_read_state -- u, I (fp32) and refractory counters of instance k,
+ * n_neurons entries each; any pointer may be NULL.  Synchronises. */
+int snn_batch_read_state(snn_batch* b, int32_t k, float* u_host, float* i_syn_host,
+                         int32_t* refr_host);
+
+/* snn_batch_counters -- steps taken, spikes and synaptic events of instance k. */
+int snn_batch_counters(snn_batch* b, int32_t k, int64_t* step, uint64_t* spikes,
+                       uint64_t* events);
+
+int snn_batch_get_info(snn_batch* b, int32_t k, snn_batch_info* info);
+
+/* snn_batch_set_tiling -- override the autotuner's delivery tiling of
+ * instance k (0 one warp per spike, 1 one CTA per row) for the steps issued
+ * after the call.  Results do not depend on the tiling.  Synchronises. */
+int snn_batch_set_tiling(snn_batch* b, int32_t k, int32_t tiling);
+
+/* snn_batch_destroy -- free all device memory of the batch (synchronises). */
+int snn_batch_destroy(snn_batch* b);
+
 /* snn_destroy -- free all device memory of the network (synchronises). */
 int snn_destroy(snn_net* net);
 

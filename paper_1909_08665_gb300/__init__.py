@@ -86,11 +86,23 @@ class SnnNoallocIO(C.Structure):
                 ("status", C.c_void_p)]
 
 
+class SnnBatchInfo(C.Structure):
+    _fields_ = [("n_instances", C.c_int32), ("n_neurons_total", C.c_int32),
+                ("n_neurons", C.c_int32), ("n_synapses", C.c_int64), ("tiling", C.c_int32),
+                ("tune_us_warp", C.c_float), ("tune_us_block", C.c_float),
+                ("blocks", C.c_int32), ("threads", C.c_int32),
+                ("neurons_per_thread", C.c_int32), ("graph", C.c_int32),
+                ("graph_steps", C.c_int32)]
+
+
 NOALLOC_MAX_NEURONS = 131072
 
 EXPORTED = ["snn_create", "snn_create_from_rows", "snn_step", "snn_sync", "snn_read_spikes",
             "snn_raster_size", "snn_read_state", "snn_read_ring", "snn_counters", "snn_get_info",
-            "snn_export_network", "snn_deliver", "snn_step_noalloc", "snn_destroy",
+            "snn_export_network", "snn_deliver", "snn_step_noalloc", "snn_batch_create",
+            "snn_batch_step", "snn_batch_sync", "snn_batch_read_spikes", "snn_batch_read_state",
+            "snn_batch_counters", "snn_batch_get_info", "snn_batch_set_tiling",
+            "snn_batch_destroy", "snn_destroy",
             "snn_last_error"]
 
 _lib = None
@@ -122,6 +134,19 @@ def lib():
         L.snn_deliver.argtypes = [vp, vp, C.c_int32, C.c_int64, C.c_int32]
         L.snn_step_noalloc.argtypes = [P(SnnConfig), C.c_uint64, P(SnnNoallocIO), C.c_int64,
                                        C.c_int64, vp]
+        L.snn_batch_create.argtypes = [P(SnnConfig), P(C.c_uint64), C.c_int32, P(SnnOptions),
+                                       vp, P(vp)]
+        L.snn_batch_step.argtypes = [vp, C.c_int64]
+        L.snn_batch_sync.argtypes = [vp]
+        L.snn_batch_read_spikes.argtypes = [vp, C.c_int32, P(C.c_uint32), P(C.c_uint32),
+                                            C.c_int64, P(C.c_int64)]
+        L.snn_batch_read_state.argtypes = [vp, C.c_int32, P(C.c_float), P(C.c_float),
+                                           P(C.c_int32)]
+        L.snn_batch_counters.argtypes = [vp, C.c_int32, P(C.c_int64), P(C.c_uint64),
+                                         P(C.c_uint64)]
+        L.snn_batch_get_info.argtypes = [vp, C.c_int32, P(SnnBatchInfo)]
+        L.snn_batch_set_tiling.argtypes = [vp, C.c_int32, C.c_int32]
+        L.snn_batch_destroy.argtypes = [vp]
         L.snn_destroy.argtypes = [vp]
         L.snn_last_error.restype = C.c_char_p
         for name in EXPORTED:
@@ -284,6 +309,84 @@ class Microcircuit:
     def close(self):
         if getattr(self, "_h", None):
             lib().snn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MicrocircuitBatch:
+    """Many independent networks (own configuration and seed each) stepped
+    together by one persistent kernel replayed from a CUDA graph."""
+
+    def __init__(self, cfgs: list, seeds: list | None = None, raster_capacity: int = 0,
+                 timeout_s: float = 0.0, stream=None, inject_fault: int = 0):
+        if not cfgs:
+            raise ValueError("at least one configuration")
+        self.cfgs = list(cfgs)
+        self.seeds = [int(c["seed"]) for c in cfgs] if seeds is None else [int(x) for x in seeds]
+        if len(self.seeds) != len(self.cfgs):
+            raise ValueError("one seed per configuration")
+        arr = (SnnConfig * len(cfgs))(*[make_config(c) for c in cfgs])
+        sd = np.ascontiguousarray(self.seeds, np.uint64)
+        self._o = SnnOptions(0, int(inject_fault), int(raster_capacity), float(timeout_s))
+        self.sizes = [int(sum(c["pop_sizes"])) for c in cfgs]
+        self.stream = _stream_handle(stream)
+        h = C.c_void_p()
+        _check(lib().snn_batch_create(arr, _ptr(sd, C.c_uint64), len(cfgs), C.byref(self._o),
+                                      self.stream, C.byref(h)))
+        self._h = h
+
+    def __len__(self):
+        return len(self.cfgs)
+
+    def step(self, n_steps: int):
+        _check(lib().snn_batch_step(self._h, int(n_steps)))
+
+    def sync(self):
+        _check(lib().snn_batch_sync(self._h))
+
+    def set_tiling(self, k: int, tiling: int):
+        _check(lib().snn_batch_set_tiling(self._h, int(k), int(tiling)))
+
+    def info(self, k: int = 0) -> dict:
+        i = SnnBatchInfo()
+        _check(lib().snn_batch_get_info(self._h, int(k), C.byref(i)))
+        return {f: getattr(i, f) for f, _ in SnnBatchInfo._fields_}
+
+    def read_spikes(self, k: int, cap: int | None = None):
+        """Drain instance k's spikes; returns (steps, ids) sorted by (step, id)."""
+        if cap is None:                     # spikes so far bound the undrained ones
+            cap = max(1, self.counters(k)["spikes"])
+        st = np.zeros(cap, np.uint32)
+        ids = np.zeros(cap, np.uint32)
+        n = C.c_int64()
+        _check(lib().snn_batch_read_spikes(self._h, int(k), _ptr(st, C.c_uint32),
+                                           _ptr(ids, C.c_uint32), int(cap), C.byref(n)))
+        st, ids = st[:n.value], ids[:n.value]
+        order = np.lexsort((ids, st))
+        return st[order].astype(np.int64), ids[order].astype(np.int64)
+
+    def state(self, k: int):
+        n = self.sizes[k]
+        u = np.zeros(n, np.float32)
+        i = np.zeros(n, np.float32)
+        r = np.zeros(n, np.int32)
+        _check(lib().snn_batch_read_state(self._h, int(k), _ptr(u, C.c_float),
+                                          _ptr(i, C.c_float), _ptr(r, C.c_int32)))
+        return u, i, r
+
+    def counters(self, k: int) -> dict:
+        s, a, b = C.c_int64(), C.c_uint64(), C.c_uint64()
+        _check(lib().snn_batch_counters(self._h, int(k), C.byref(s), C.byref(a), C.byref(b)))
+        return {"step": s.value, "spikes": a.value, "events": b.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().snn_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

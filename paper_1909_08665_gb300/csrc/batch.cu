@@ -1,0 +1,893 @@
+// batch.cu -- many independent microcircuits of uneven size and seed in one
+// persistent kernel (the same method as the single network: Sec. 2.1 Eq. 1,
+// Sec. 3.1.2 ring buffers, Sec. 3.1.3 per-step processing), replayed from a
+// captured CUDA graph.
+//
+// The neurons of all instances are concatenated: instance k owns the global
+// range [goff_k, goff_k + n_k).  CTA b owns the contiguous range
+// [b * 512 * NPT, (b + 1) * 512 * NPT) and keeps u, I and the refractory
+// counter of its neurons in registers; the four cached background draws of
+// each neuron sit in shared memory.  The 64-slot ring buffers of all neurons
+// are one global array [slot][global neuron].
+//
+// Per step t the work is A(t) (membrane update u_t with I_{t-1}, threshold,
+// reset, refractory; spikes appended to the list of step t), D(t) (delivery
+// of the spikes of step t through their rows into ring slots t + d, d >= 1)
+// and C(t) (I_t = P11 I_{t-1} + ring[t] + background).  A(t + 1) needs only
+// I_t, and C(t) needs the deliveries of step t - 1, so one grid barrier per
+// step suffices:
+//     A(t0);  for t: { barrier; D(t); C(t); A(t + 1) }
+// D(t) writes slots t + 1 .. t + 63 while C(t) reads slot t; the lists and
+// their counters rotate over 2 and 4 step parities, so each buffer is reset
+// or rewritten only after the barrier that ends its last reader's phase.
+// Every result equals the single-network path bit for bit (same fp32
+// operation order, integer accumulation, same random counters).
+//
+// Delivery tiling per instance: one warp per spike (tiling 0) or one CTA per
+// row (tiling 1).  The autotuner (host side, at creation) times both on each
+// instance's own rows with a seeded spike list of the instance's expected
+// size and keeps the faster one.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/snn.h"
+#include "snn_internal.cuh"
+
+namespace snn {
+
+int host_tables(const snn_config* cfg, HostTables* out);
+int build_rows_device(const snn_config* cfg, uint64_t seed, cudaStream_t stream,
+                      unsigned long long** row_start, uint32_t** words, uint64_t* nnz);
+int set_error(int code, const char* msg);
+int set_cuda_error(cudaError_t e, const char* what);
+
+namespace {
+
+constexpr int kBThreads = 512;
+constexpr int kBWarps = kBThreads / 32;
+constexpr int kMaxInst = 1024;
+constexpr int kGraphChunk = 1000;       // steps per captured launch
+constexpr int kWarpUnroll = 8;          // words in flight per lane, warp tiling
+constexpr int kBlockUnroll = 4;         // words in flight per thread, CTA tiling
+constexpr uint32_t kBatchRasterOverflow = 2u;
+
+// per-instance constants read in the neuron phases (one 48-byte record)
+struct __align__(16) InstHot {
+    float4 prop;                        // P22, P21, P11, theta
+    int4 misc;                          // n_ref, mode, wext_q, goff
+    uint4 key;                          // key0, key1, tiling, n
+};
+
+// per-instance data read in the delivery phase
+struct InstCold {
+    int32_t pop_start[kMaxPop + 1];
+    int32_t n_pop, goff, n, pad;
+    const unsigned long long* row_start;
+    const uint32_t* words;
+    const int32_t* wtab;                // [8 target pops][8 source pops][128 codes]
+};
+
+struct BatchParams {
+    int32_t n_inst, ntot, n_steps;
+    int32_t inject_fault;               // 1: CTA 0 never arrives at a barrier
+    uint64_t timeout_ns;
+    const InstHot* hot;
+    const InstCold* cold;
+    const uint32_t* pois;               // [n_inst][8][32] thresholds minus one
+    const float* cdc;                   // [n_inst][8] P20 * I_DC
+    const int32_t* goff;                // [n_inst + 1]
+    float* u;
+    float* i_syn;
+    int32_t* refr;
+    int32_t* ring;                      // [64][ntot]
+    uint32_t* list;                     // [2 parity][2 tiling][ntot] global ids
+    uint32_t* cnt;                      // [4 parity][2 tiling]
+    uint32_t* ras_step;
+    uint32_t* ras_id;
+    uint32_t* ras_n;
+    uint32_t ras_cap;
+    unsigned long long* inst_counters;  // [n_inst][2] spikes, events
+    long long* step;                    // device step counter
+    uint32_t* barrier;
+    uint32_t* status;
+    uint32_t* abort_flag;
+};
+
+__device__ __forceinline__ int inst_of(const int32_t* s_goff, int n_inst, int32_t gi) {
+    int a = 0, b = n_inst;              // s_goff[a] <= gi < s_goff[b]
+    while (b - a > 1) {
+        const int m = (a + b) >> 1;
+        if (s_goff[m] <= gi) a = m;
+        else b = m;
+    }
+    return a;
+}
+
+// full grid barrier on a monotonic counter (reset before every launch);
+// the wait is bounded by time and by the abort flag
+__device__ bool grid_sync(const BatchParams& p, uint32_t& gen, volatile uint32_t* s_abort) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (!(p.inject_fault == 1 && blockIdx.x == 0)) atomicAdd(p.barrier, 1u);
+        const uint32_t target = (gen + 1u) * gridDim.x;
+        const uint64_t t_start = globaltimer_ns();
+        uint32_t iter = 0;
+        while (ld_acquire_gpu(p.barrier) < target) {
+            if ((++iter & 255u) == 0u) {
+                if (ld_relaxed_gpu(p.abort_flag) != 0u) { *s_abort = 1u; break; }
+                if (globaltimer_ns() - t_start > p.timeout_ns) {
+                    atomicOr(p.status, kStatusTimeout);
+                    atomicExch(p.abort_flag, 1u);
+                    *s_abort = 1u;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    ++gen;
+    return *s_abort == 0u;
+}
+
+// Row of global neuron gi, emitted at step t, added into ring slots t + d by
+// `lanes` cooperating threads (rank r among them), U words in flight each.
+template <int U>
+__device__ __forceinline__ void deliver_row(const BatchParams& p, const int32_t* s_goff, int32_t gi,
+                                            long long t, int r, int lanes, bool count) {
+    const int ki = inst_of(s_goff, p.n_inst, gi);
+    const InstCold& I = p.cold[ki];
+    const int32_t j = gi - I.goff;
+    const int n_pop = I.n_pop;
+    int32_t ps[kMaxPop];
+#pragma unroll
+    for (int k = 1; k < kMaxPop; ++k) ps[k] = k < n_pop ? I.pop_start[k] : 0x7fffffff;
+    int q = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxPop; ++k) q += j >= ps[k] ? 1 : 0;
+    const int32_t* wq = I.wtab + q * kWCodes;
+    const uint32_t* words = I.words;
+    int32_t* rbase = p.ring + I.goff;
+    const size_t ntot = (size_t)p.ntot;
+    const unsigned long long b = I.row_start[j], e = I.row_start[j + 1];
+    for (unsigned long long base = b + r; base < e; base += (unsigned long long)lanes * U) {
+        uint32_t w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned long long idx = base + (unsigned long long)u * lanes;
+            w[u] = idx < e ? __ldg(&words[idx]) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (base + (unsigned long long)u * lanes < e) {
+                const int32_t tgt = (int32_t)(w[u] & kTgtMask);
+                int pp = 0;
+#pragma unroll
+                for (int k = 1; k < kMaxPop; ++k) pp += tgt >= ps[k] ? 1 : 0;
+                const int32_t wt = __ldg(&wq[pp * (kMaxPop * kWCodes) + (int)(w[u] >> 25)]);
+                const uint32_t slot = (uint32_t)(t + ((w[u] >> kTgtBits) & 63u)) & (kRing - 1);
+                atomicAdd(&rbase[(size_t)slot * ntot + tgt], wt);
+            }
+        }
+    }
+    if (count && r == 0) atomicAdd(&p.inst_counters[ki * 2 + 1], e - b);
+}
+
+template <int NPT>
+__global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ BatchParams p) {
+    extern __shared__ uint32_t s_rnd[];            // [NPT][4 draws][kBThreads]
+    __shared__ int32_t s_goff[kMaxInst + 1];
+    __shared__ volatile uint32_t s_abort;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int k = tid; k <= p.n_inst; k += kBThreads) s_goff[k] = p.goff[k];
+    if (tid == 0) s_abort = 0u;
+    __syncthreads();
+    const int32_t gbase = (int32_t)blockIdx.x * (kBThreads * NPT) + tid;
+    const long long t0 = *p.step;
+    const int n = p.n_steps;
+    const size_t ntot = (size_t)p.ntot;
+
+    float u[NPT], isyn[NPT];
+    int32_t refr[NPT], ip[NPT];                     // ip = instance << 3 | population
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int32_t gi = gbase + k * kBThreads;
+        u[k] = 0.f; isyn[k] = 0.f; refr[k] = 0; ip[k] = -1;
+        if (gi < p.ntot) {
+            u[k] = p.u[gi];
+            isyn[k] = p.i_syn[gi];
+            refr[k] = p.refr[gi];
+            const int ki = inst_of(s_goff, p.n_inst, gi);
+            const InstCold& I = p.cold[ki];
+            ip[k] = (ki << 3) | pop_index(I.pop_start, I.n_pop, gi - I.goff);
+        }
+    }
+    // per-thread cache of the constants of the last instance seen
+    int cinst = -1;
+    float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
+    int4 pm = make_int4(0, 0, 0, 0);
+    uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+    auto fetch = [&](int ki) {
+        if (ki != cinst) {
+            cinst = ki;
+            pf = p.hot[ki].prop;
+            pm = p.hot[ki].misc;
+            pk = p.hot[ki].key;
+        }
+    };
+
+    // A(t): membrane, threshold, reset, refractory; spikes into the lists
+    auto phase_a = [&](long long t) {
+        const uint32_t par4 = (uint32_t)(t & 3), par2 = (uint32_t)(t & 1);
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int32_t gi = gbase + k * kBThreads;
+            bool spk = false;
+            int tiling = 0;
+            if (ip[k] >= 0) {
+                fetch(ip[k] >> 3);
+                if (refr[k] > 0) {
+                    refr[k] -= 1;
+                    u[k] = 0.f;
+                } else {
+                    float v = __fadd_rn(__fmul_rn(pf.x, u[k]), __fmul_rn(pf.y, isyn[k]));
+                    if (pm.y == 1) v = __fadd_rn(v, __ldg(&p.cdc[ip[k]]));
+                    u[k] = v;
+                }
+                if (u[k] > pf.w) {
+                    spk = true;
+                    u[k] = 0.f;
+                    refr[k] = pm.x;
+                }
+                tiling = (int)pk.z;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, spk);
+            if (m) {
+                const unsigned mb = __ballot_sync(0xffffffffu, spk && tiling == 1);
+                const unsigned mw = m & ~mb;
+                uint32_t bw = 0, bb = 0, br = 0;
+                if (lane == 0) {
+                    if (mw) bw = atomicAdd(&p.cnt[par4 * 2 + 0], (uint32_t)__popc(mw));
+                    if (mb) bb = atomicAdd(&p.cnt[par4 * 2 + 1], (uint32_t)__popc(mb));
+                    br = atomicAdd(p.ras_n, (uint32_t)__popc(m));
+                }
+                bw = __shfl_sync(0xffffffffu, bw, 0);
+                bb = __shfl_sync(0xffffffffu, bb, 0);
+                br = __shfl_sync(0xffffffffu, br, 0);
+                if (spk) {
+                    const unsigned lt = (1u << lane) - 1u;
+                    const uint32_t pos = tiling ? bb + (uint32_t)__popc(mb & lt)
+                                                : bw + (uint32_t)__popc(mw & lt);
+                    p.list[((size_t)par2 * 2 + (uint32_t)tiling) * ntot + pos] = (uint32_t)gi;
+                    const uint32_t rp = br + (uint32_t)__popc(m & lt);
+                    if (rp < p.ras_cap) {
+                        p.ras_step[rp] = (uint32_t)t;
+                        p.ras_id[rp] = (uint32_t)gi;
+                    } else {
+                        atomicOr(p.status, kBatchRasterOverflow);
+                    }
+                    atomicAdd(&p.inst_counters[(ip[k] >> 3) * 2], 1ull);
+                }
+            }
+        }
+    };
+
+    if (n > 0) phase_a(t0);
+    uint32_t gen = 0;
+    for (int s = 0; s < n; ++s) {
+        const long long t = t0 + s;
+        if (!grid_sync(p, gen, &s_abort)) break;
+        // counters of step t + 2: last read in D(t - 2), next written in A(t + 2)
+        if (blockIdx.x == 0 && tid < 2) p.cnt[(uint32_t)((t + 2) & 3) * 2 + tid] = 0u;
+
+        // ---- D(t): spikes of step t ----
+        {
+            const uint32_t par4 = (uint32_t)(t & 3), par2 = (uint32_t)(t & 1);
+            const uint32_t nw = __ldcg(&p.cnt[par4 * 2 + 0]);
+            const uint32_t nb = __ldcg(&p.cnt[par4 * 2 + 1]);
+            const uint32_t* lw = p.list + ((size_t)par2 * 2 + 0) * ntot;
+            const uint32_t* lb = p.list + ((size_t)par2 * 2 + 1) * ntot;
+            // warp w of CTA b takes spikes w * grid + b, spreading them over SMs
+            for (uint32_t k = (uint32_t)(tid >> 5) * gridDim.x + blockIdx.x; k < nw;
+                 k += (uint32_t)kBWarps * gridDim.x)
+                deliver_row<kWarpUnroll>(p, s_goff, (int32_t)__ldcg(&lw[k]), t, lane, 32, true);
+            // CTA rows start from the last CTA, away from the first warp rows
+            for (uint32_t k = gridDim.x - 1u - blockIdx.x; k < nb; k += gridDim.x)
+                deliver_row<kBlockUnroll>(p, s_goff, (int32_t)__ldcg(&lb[k]), t, tid, kBThreads, true);
+        }
+
+        // ---- C(t): ring slot t, background, synaptic current ----
+        {
+            const uint32_t slot = (uint32_t)t & (kRing - 1);
+            int32_t* rs = p.ring + (size_t)slot * ntot;
+            int32_t acc[NPT];
+#pragma unroll
+            for (int k = 0; k < NPT; ++k)
+                acc[k] = ip[k] >= 0 ? __ldcg(&rs[gbase + k * kBThreads]) : 0;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k)
+                if (ip[k] >= 0) __stcg(&rs[gbase + k * kBThreads], 0);
+            const bool refresh = (t & 3) == 0 || s == 0;
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                if (ip[k] < 0) continue;
+                fetch(ip[k] >> 3);
+                if (pm.y == 0) {
+                    uint32_t* rr = s_rnd + (k * 4) * kBThreads + tid;
+                    if (refresh) {
+                        const uint32_t li = (uint32_t)(gbase + k * kBThreads - pm.w);
+                        const uint4 r = philox(make_uint4(li, (uint32_t)(t >> 2), kStreamPois,
+                                                          (uint32_t)(t >> 34)), pk.x, pk.y);
+                        rr[0] = r.x;
+                        rr[kBThreads] = r.y;
+                        rr[2 * kBThreads] = r.z;
+                        rr[3 * kBThreads] = r.w;
+                    }
+                    const uint32_t x = rr[(int)(t & 3) * kBThreads];
+                    // k = #{m : x >= T_m} = #{m : x > T_m - 1}; thresholds
+                    // ascend, so the tail beyond 12 matters only if all 12 pass
+                    const uint4* th = reinterpret_cast<const uint4*>(p.pois) + (size_t)ip[k] * (kPoisTable / 4);
+                    const uint4 a0 = __ldg(&th[0]), a1 = __ldg(&th[1]), a2 = __ldg(&th[2]);
+                    int kk = (x > a0.x) + (x > a0.y) + (x > a0.z) + (x > a0.w) +
+                             (x > a1.x) + (x > a1.y) + (x > a1.z) + (x > a1.w) +
+                             (x > a2.x) + (x > a2.y) + (x > a2.z) + (x > a2.w);
+                    if (kk == 12) {
+                        const uint32_t* tt = p.pois + (size_t)ip[k] * kPoisTable;
+                        for (int mm = 12; mm < kPoisTable; ++mm) kk += x > __ldg(&tt[mm]) ? 1 : 0;
+                    }
+                    acc[k] += kk * pm.z;
+                }
+                isyn[k] = __fadd_rn(__fmul_rn(pf.z, isyn[k]),
+                                    __fmul_rn(__int2float_rn(acc[k]), 0.00390625f));
+            }
+        }
+        // ---- A(t + 1) ----
+        if (s + 1 < n) phase_a(t + 1);
+    }
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int32_t gi = gbase + k * kBThreads;
+        if (ip[k] >= 0) {
+            p.u[gi] = u[k];
+            p.i_syn[gi] = isyn[k];
+            p.refr[gi] = refr[k];
+        }
+    }
+    if (blockIdx.x == 0 && tid == 0 && s_abort == 0u) *p.step = t0 + n;
+}
+
+// autotuner probe: deliver `n` spikes (global ids) with one tiling at step 0
+__global__ void __launch_bounds__(kBThreads) k_probe_deliver(const __grid_constant__ BatchParams p,
+                                                             const uint32_t* spikes, int n,
+                                                             int tiling) {
+    __shared__ int32_t s_goff[kMaxInst + 1];
+    for (int k = threadIdx.x; k <= p.n_inst; k += kBThreads) s_goff[k] = p.goff[k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    if (tiling == 0) {
+        const int warps = (int)gridDim.x * kBWarps;
+        for (int k = (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x; k < n; k += warps)
+            deliver_row<kWarpUnroll>(p, s_goff, (int32_t)spikes[k], 0, lane, 32, false);
+    } else {
+        for (int k = blockIdx.x; k < n; k += gridDim.x)
+            deliver_row<kBlockUnroll>(p, s_goff, (int32_t)spikes[k], 0, threadIdx.x, kBThreads, false);
+    }
+}
+
+constexpr int kNptVariants[] = {1, 2, 4, 6, 8, 12, 16};
+
+template <int NPT>
+const void* batch_fn() { return reinterpret_cast<const void*>(&k_batch<NPT>); }
+
+const void* select_batch(int npt) {
+    switch (npt) {
+        case 1: return batch_fn<1>();
+        case 2: return batch_fn<2>();
+        case 4: return batch_fn<4>();
+        case 6: return batch_fn<6>();
+        case 8: return batch_fn<8>();
+        case 12: return batch_fn<12>();
+        case 16: return batch_fn<16>();
+        default: return nullptr;
+    }
+}
+
+size_t batch_smem(int npt) { return (size_t)npt * 4 * kBThreads * sizeof(uint32_t); }
+
+}  // namespace
+}  // namespace snn
+
+using namespace snn;
+
+struct snn_batch {
+    int n_inst = 0;
+    int ntot = 0;
+    int npt = 0;
+    int blocks = 0;
+    size_t smem = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<int32_t> goff;
+    std::vector<InstHot> hot_h;
+    std::vector<InstCold> cold_h;
+    std::vector<uint64_t> nnz;
+    std::vector<float> tune_us[2];
+    std::vector<unsigned long long*> row_start;
+    std::vector<uint32_t*> words;
+    std::vector<int32_t*> wtab;
+    BatchParams p;
+    InstHot* d_hot = nullptr;
+    InstCold* d_cold = nullptr;
+    uint32_t* d_pois = nullptr;
+    float* d_cdc = nullptr;
+    int32_t* d_goff = nullptr;
+    float* d_u = nullptr;
+    float* d_i = nullptr;
+    int32_t* d_r = nullptr;
+    int32_t* d_ring = nullptr;
+    uint32_t* d_list = nullptr;
+    uint32_t* d_cnt = nullptr;
+    uint32_t* d_ras_step = nullptr;
+    uint32_t* d_ras_id = nullptr;
+    uint32_t* d_ras_n = nullptr;
+    uint32_t ras_cap = 0;
+    unsigned long long* d_ic = nullptr;
+    long long* d_step = nullptr;
+    uint32_t* d_sync = nullptr;          // [0] barrier, [1] status, [2] abort
+    cudaGraphExec_t graph = nullptr;
+    bool graph_ok = false;
+    long long step = 0;
+    std::vector<std::vector<uint32_t>> host_steps, host_ids;   // drained raster per instance
+};
+
+namespace {
+
+template <typename T>
+int balloc(T** p, size_t n, const char* what) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_error(SNN_ERR_OOM, what);
+    }
+    return SNN_OK;
+}
+
+#define BCALL(x)                           \
+    do {                                   \
+        int rc_ = (x);                     \
+        if (rc_ != SNN_OK) return rc_;     \
+    } while (0)
+#define BCK(call)                                                   \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return set_cuda_error(e_, #call);    \
+    } while (0)
+
+void free_batch(snn_batch* b) {
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto* x : b->row_start) cudaFree(x);
+    for (auto* x : b->words) cudaFree(x);
+    for (auto* x : b->wtab) cudaFree(x);
+    void* ptrs[] = {b->d_hot, b->d_cold, b->d_pois, b->d_cdc, b->d_goff, b->d_u, b->d_i,
+                    b->d_r, b->d_ring, b->d_list, b->d_cnt, b->d_ras_step, b->d_ras_id,
+                    b->d_ras_n, b->d_ic, b->d_step, b->d_sync};
+    for (void* x : ptrs)
+        if (x) cudaFree(x);
+    delete b;
+}
+
+cudaError_t launch_batch(snn_batch* b, int n_steps) {
+    BatchParams p = b->p;
+    p.n_steps = n_steps;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->blocks);
+    cfg.blockDim = dim3(kBThreads);
+    cfg.dynamicSmemBytes = b->smem;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {&p};
+    cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(uint32_t), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync + 2, 0, sizeof(uint32_t), b->stream);
+    if (e == cudaSuccess) e = cudaLaunchKernelExC(&cfg, select_batch(b->npt), args);
+    return e;
+}
+
+// time both tilings on each instance's own rows; keep the faster
+int autotune(snn_batch* b) {
+    cudaStream_t s = b->stream;
+    constexpr int kMaxProbe = 1 << 14;
+    uint32_t* d_spk = nullptr;
+    BCALL(balloc(&d_spk, kMaxProbe, "autotune spikes"));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    b->tune_us[0].assign(b->n_inst, 0.f);
+    b->tune_us[1].assign(b->n_inst, 0.f);
+    for (int k = 0; k < b->n_inst && e == cudaSuccess; ++k) {
+        const InstCold& I = b->cold_h[k];
+        // about 5 Hz of activity in one 0.1 ms step, at least 4 spikes
+        const int n = std::min(kMaxProbe, std::max(4, (int)(I.n * 5e-4 + 0.5)));
+        std::vector<uint32_t> spk(n);
+        uint64_t x = 0x9E3779B97F4A7C15ull * (uint64_t)(k + 1);
+        for (int i = 0; i < n; ++i) {
+            x ^= x >> 12;
+            x ^= x << 25;
+            x ^= x >> 27;
+            spk[i] = (uint32_t)(I.goff + (int)((x * 0x2545F4914F6CDD1Dull) % (uint64_t)I.n));
+        }
+        e = cudaMemcpyAsync(d_spk, spk.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s);
+        for (int tl = 0; tl < 2 && e == cudaSuccess; ++tl) {
+            const int grid = tl == 0 ? std::min(b->blocks, std::max(1, (n + kBWarps - 1) / kBWarps))
+                                     : std::min(b->blocks, n);
+            float best = 1e30f;
+            for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+                cudaEventRecord(e0, s);
+                k_probe_deliver<<<grid, kBThreads, 0, s>>>(b->p, d_spk, n, tl);
+                cudaEventRecord(e1, s);
+                e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) best = std::min(best, ms);
+            }
+            b->tune_us[tl][k] = best * 1000.f;
+        }
+        b->hot_h[k].key.z = b->tune_us[1][k] < b->tune_us[0][k] ? 1u : 0u;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d_spk);
+    if (e != cudaSuccess) return set_cuda_error(e, "autotune");
+    // the probes added into the ring: clear it again
+    BCK(cudaMemsetAsync(b->d_ring, 0, sizeof(int32_t) * (size_t)kRing * b->ntot, s));
+    BCK(cudaMemcpyAsync(b->d_hot, b->hot_h.data(), sizeof(InstHot) * b->n_inst,
+                        cudaMemcpyHostToDevice, s));
+    BCK(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+int drain_raster(snn_batch* b) {
+    BCK(cudaStreamSynchronize(b->stream));
+    uint32_t n = 0;
+    BCK(cudaMemcpy(&n, b->d_ras_n, sizeof(n), cudaMemcpyDeviceToHost));
+    const uint32_t m = std::min(n, b->ras_cap);
+    std::vector<uint32_t> st(m), id(m);
+    if (m) {
+        BCK(cudaMemcpy(st.data(), b->d_ras_step, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost));
+        BCK(cudaMemcpy(id.data(), b->d_ras_id, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost));
+    }
+    BCK(cudaMemset(b->d_ras_n, 0, sizeof(uint32_t)));
+    for (uint32_t r = 0; r < m; ++r) {
+        const int k = (int)(std::upper_bound(b->goff.begin(), b->goff.end(), (int32_t)id[r]) -
+                            b->goff.begin()) - 1;
+        b->host_steps[k].push_back(st[r]);
+        b->host_ids[k].push_back(id[r] - (uint32_t)b->goff[k]);
+    }
+    if (n > b->ras_cap) return set_error(SNN_ERR_OVERFLOW, "batch raster capacity exceeded");
+    return SNN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_inst,
+                     const snn_options* opt, void* stream, snn_batch** out) {
+    if (!cfgs || !seeds || !out || n_inst < 1 || n_inst > kMaxInst)
+        return set_error(SNN_ERR_INVALID, "need 1..1024 configurations, seeds and out");
+    *out = nullptr;
+    int dev = 0;
+    BCK(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    BCK(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10 || prop.minor != 3)
+        return set_error(SNN_ERR_UNSUPPORTED, "this library is built for sm_103 (GB300) GPUs only");
+    snn_batch* b = new snn_batch();
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    cudaStream_t s = b->stream;
+    b->n_inst = n_inst;
+    b->goff.assign(n_inst + 1, 0);
+    b->hot_h.resize(n_inst);
+    b->cold_h.resize(n_inst);
+    b->nnz.resize(n_inst);
+    b->host_steps.resize(n_inst);
+    b->host_ids.resize(n_inst);
+    std::vector<uint32_t> pois((size_t)n_inst * kMaxPop * kPoisTable, 0xffffffffu);
+    std::vector<float> cdc((size_t)n_inst * kMaxPop, 0.f);
+    int rc = SNN_OK;
+    long long ntot = 0;
+    for (int k = 0; k < n_inst && rc == SNN_OK; ++k) {
+        HostTables ht;
+        rc = host_tables(&cfgs[k], &ht);
+        if (rc != SNN_OK) break;
+        InstHot& H = b->hot_h[k];
+        InstCold& C = b->cold_h[k];
+        std::memset(&H, 0, sizeof(H));
+        std::memset(&C, 0, sizeof(C));
+        H.prop = make_float4(ht.prop[0], ht.prop[1], ht.prop[2], ht.theta);
+        H.misc = make_int4(ht.n_ref, ht.mode, ht.wext_q, (int32_t)ntot);
+        H.key = make_uint4((uint32_t)(seeds[k] & 0xffffffffu), (uint32_t)(seeds[k] >> 32), 0u,
+                           (uint32_t)ht.n);
+        for (int q = 0; q <= kMaxPop; ++q) C.pop_start[q] = ht.pop_start[q];
+        C.n_pop = ht.n_pop;
+        C.goff = (int32_t)ntot;
+        C.n = ht.n;
+        for (int q = 0; q < kMaxPop; ++q) {
+            cdc[(size_t)k * kMaxPop + q] = ht.cdc[q];
+            for (int m = 0; m < kPoisTable; ++m)
+                pois[((size_t)k * kMaxPop + q) * kPoisTable + m] = (uint32_t)(ht.pois[q][m] - 1u);
+        }
+        unsigned long long* rs = nullptr;
+        uint32_t* wd = nullptr;
+        uint64_t nnz = 0;
+        rc = build_rows_device(&cfgs[k], seeds[k], s, &rs, &wd, &nnz);
+        if (rc != SNN_OK) break;
+        b->row_start.push_back(rs);
+        b->words.push_back(wd);
+        b->nnz[k] = nnz;
+        int32_t* wt = nullptr;
+        rc = balloc(&wt, kMaxPop * kMaxPop * kWCodes, "batch weight table");
+        if (rc != SNN_OK) break;
+        b->wtab.push_back(wt);
+        const cudaError_t ce = cudaMemcpy(wt, ht.wtab, sizeof(ht.wtab), cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) {
+            rc = set_cuda_error(ce, "weight table upload");
+            break;
+        }
+        C.row_start = rs;
+        C.words = wd;
+        C.wtab = wt;
+        ntot += ht.n;
+        b->goff[k + 1] = (int32_t)ntot;
+        if (ntot > (1ll << 30)) rc = set_error(SNN_ERR_INVALID, "too many neurons in the batch");
+    }
+    if (rc != SNN_OK) {
+        free_batch(b);
+        return rc;
+    }
+    b->ntot = (int)ntot;
+    // launch shape: one CTA per SM, the fewest neurons per thread that cover the batch
+    b->blocks = prop.multiProcessorCount;
+    b->npt = 0;
+    for (int npt : kNptVariants) {
+        if ((long long)npt * kBThreads * b->blocks < ntot) continue;
+        const size_t smem = batch_smem(npt);
+        if (cudaFuncSetAttribute(select_batch(npt), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            break;
+        int ps = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, select_batch(npt), kBThreads, smem) !=
+                cudaSuccess ||
+            ps < 1)
+            break;
+        b->npt = npt;
+        b->smem = smem;
+        break;
+    }
+    cudaGetLastError();
+    if (b->npt == 0) {
+        free_batch(b);
+        return set_error(SNN_ERR_UNSUPPORTED, "batch too large for one co-resident grid");
+    }
+    const long long cap = (opt && opt->raster_capacity > 0) ? opt->raster_capacity : (64ll << 20);
+    b->ras_cap = (uint32_t)std::min<long long>(cap, 0x7fffffff);
+    if (rc == SNN_OK) rc = balloc(&b->d_hot, n_inst, "batch instance constants");
+    if (rc == SNN_OK) rc = balloc(&b->d_cold, n_inst, "batch instance rows");
+    if (rc == SNN_OK) rc = balloc(&b->d_pois, pois.size(), "batch background tables");
+    if (rc == SNN_OK) rc = balloc(&b->d_cdc, cdc.size(), "batch DC input");
+    if (rc == SNN_OK) rc = balloc(&b->d_goff, n_inst + 1, "batch offsets");
+    if (rc == SNN_OK) rc = balloc(&b->d_u, ntot, "batch u");
+    if (rc == SNN_OK) rc = balloc(&b->d_i, ntot, "batch I");
+    if (rc == SNN_OK) rc = balloc(&b->d_r, ntot, "batch refractory counters");
+    if (rc == SNN_OK) rc = balloc(&b->d_ring, (size_t)kRing * ntot, "batch ring buffers");
+    if (rc == SNN_OK) rc = balloc(&b->d_list, (size_t)4 * ntot, "batch spike lists");
+    if (rc == SNN_OK) rc = balloc(&b->d_cnt, 8, "batch list counters");
+    if (rc == SNN_OK) rc = balloc(&b->d_ras_step, b->ras_cap, "batch raster");
+    if (rc == SNN_OK) rc = balloc(&b->d_ras_id, b->ras_cap, "batch raster");
+    if (rc == SNN_OK) rc = balloc(&b->d_ras_n, 1, "batch raster count");
+    if (rc == SNN_OK) rc = balloc(&b->d_ic, (size_t)2 * n_inst, "batch counters");
+    if (rc == SNN_OK) rc = balloc(&b->d_step, 1, "batch step");
+    if (rc == SNN_OK) rc = balloc(&b->d_sync, 4, "batch barrier");
+    if (rc != SNN_OK) {
+        free_batch(b);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_goff, b->goff.data(), sizeof(int32_t) * (n_inst + 1),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_hot, b->hot_h.data(), sizeof(InstHot) * n_inst, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_cold, b->cold_h.data(), sizeof(InstCold) * n_inst, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_pois, pois.data(), sizeof(uint32_t) * pois.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_cdc, cdc.data(), sizeof(float) * cdc.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_i, 0, sizeof(float) * ntot, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_r, 0, sizeof(int32_t) * ntot, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ring, 0, sizeof(int32_t) * (size_t)kRing * ntot, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cnt, 0, sizeof(uint32_t) * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ras_n, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ic, 0, sizeof(unsigned long long) * 2 * n_inst, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step, 0, sizeof(long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync, 0, sizeof(uint32_t) * 4, s);
+    for (int k = 0; k < n_inst && e == cudaSuccess; ++k) {
+        const InstHot& H = b->hot_h[k];
+        e = launch_init_state((int)H.key.w, H.key.x, H.key.y, (float)cfgs[k].u0_lo,
+                              (float)cfgs[k].u0_hi, b->d_u + H.misc.w, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return set_cuda_error(e, "batch state initialisation");
+    }
+    BatchParams& p = b->p;
+    std::memset(&p, 0, sizeof(p));
+    p.n_inst = n_inst;
+    p.ntot = b->ntot;
+    p.timeout_ns = (uint64_t)(((opt && opt->timeout_s > 0) ? opt->timeout_s : 2.0) * 1e9);
+    p.inject_fault = opt ? opt->inject_fault : 0;
+    p.hot = b->d_hot;
+    p.cold = b->d_cold;
+    p.pois = b->d_pois;
+    p.cdc = b->d_cdc;
+    p.goff = b->d_goff;
+    p.u = b->d_u;
+    p.i_syn = b->d_i;
+    p.refr = b->d_r;
+    p.ring = b->d_ring;
+    p.list = b->d_list;
+    p.cnt = b->d_cnt;
+    p.ras_step = b->d_ras_step;
+    p.ras_id = b->d_ras_id;
+    p.ras_n = b->d_ras_n;
+    p.ras_cap = b->ras_cap;
+    p.inst_counters = b->d_ic;
+    p.step = b->d_step;
+    p.barrier = b->d_sync;
+    p.status = b->d_sync + 1;
+    p.abort_flag = b->d_sync + 2;
+    rc = autotune(b);
+    if (rc != SNN_OK) {
+        free_batch(b);
+        return rc;
+    }
+    // capture one launch of kGraphChunk steps; replays advance the device
+    // step counter, so no parameter changes between replays
+    // (captured on a private stream: the legacy default stream cannot be
+    // captured; the graph is then launched on the batch's own stream)
+    cudaGraph_t g = nullptr;
+    cudaStream_t cs = nullptr;
+    b->graph_ok = false;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            b->stream = cs;
+            const cudaError_t le = launch_batch(b, kGraphChunk);
+            b->stream = s;
+            const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+            if (le == cudaSuccess && ce == cudaSuccess && g &&
+                cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess)
+                b->graph_ok = true;
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaStreamDestroy(cs);
+    }
+    cudaGetLastError();
+    *out = b;
+    return SNN_OK;
+}
+
+int snn_batch_step(snn_batch* b, int64_t n_steps) {
+    if (!b || n_steps < 0) return set_error(SNN_ERR_INVALID, "bad arguments");
+    int64_t left = n_steps;
+    while (left > 0) {
+        if (b->graph_ok && left >= kGraphChunk) {
+            BCK(cudaGraphLaunch(b->graph, b->stream));
+            left -= kGraphChunk;
+            b->step += kGraphChunk;
+        } else {
+            const int chunk = (int)std::min<int64_t>(left, 1 << 20);
+            BCK(launch_batch(b, chunk));
+            left -= chunk;
+            b->step += chunk;
+        }
+    }
+    return SNN_OK;
+}
+
+int snn_batch_sync(snn_batch* b) {
+    if (!b) return set_error(SNN_ERR_INVALID, "batch is NULL");
+    BCK(cudaStreamSynchronize(b->stream));
+    uint32_t st = 0;
+    BCK(cudaMemcpy(&st, b->d_sync + 1, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st & kStatusTimeout) return set_error(SNN_ERR_TIMEOUT, "a grid-barrier wait timed out");
+    if (st & kBatchRasterOverflow) return set_error(SNN_ERR_OVERFLOW, "batch raster capacity exceeded");
+    return SNN_OK;
+}
+
+int snn_batch_read_spikes(snn_batch* b, int32_t k, uint32_t* steps_host, uint32_t* ids_host,
+                          int64_t cap, int64_t* n) {
+    if (!b || k < 0 || k >= b->n_inst || !n || cap < 0)
+        return set_error(SNN_ERR_INVALID, "bad arguments");
+    const int rc = drain_raster(b);
+    auto& st = b->host_steps[k];
+    auto& id = b->host_ids[k];
+    const int64_t m = std::min<int64_t>(cap, (int64_t)st.size());
+    if (m > 0) {
+        if (steps_host) std::memcpy(steps_host, st.data(), sizeof(uint32_t) * m);
+        if (ids_host) std::memcpy(ids_host, id.data(), sizeof(uint32_t) * m);
+    }
+    const bool short_cap = m < (int64_t)st.size();
+    st.clear();
+    id.clear();
+    *n = m;
+    if (rc != SNN_OK) return rc;
+    if (short_cap) return set_error(SNN_ERR_OVERFLOW, "cap smaller than the recorded spikes");
+    return SNN_OK;
+}
+
+int snn_batch_read_state(snn_batch* b, int32_t k, float* u_host, float* i_syn_host,
+                         int32_t* refr_host) {
+    if (!b || k < 0 || k >= b->n_inst) return set_error(SNN_ERR_INVALID, "bad arguments");
+    BCK(cudaStreamSynchronize(b->stream));
+    const InstCold& C = b->cold_h[k];
+    if (u_host) BCK(cudaMemcpy(u_host, b->d_u + C.goff, sizeof(float) * C.n, cudaMemcpyDeviceToHost));
+    if (i_syn_host)
+        BCK(cudaMemcpy(i_syn_host, b->d_i + C.goff, sizeof(float) * C.n, cudaMemcpyDeviceToHost));
+    if (refr_host)
+        BCK(cudaMemcpy(refr_host, b->d_r + C.goff, sizeof(int32_t) * C.n, cudaMemcpyDeviceToHost));
+    return SNN_OK;
+}
+
+int snn_batch_counters(snn_batch* b, int32_t k, int64_t* step, uint64_t* spikes, uint64_t* events) {
+    if (!b || k < 0 || k >= b->n_inst) return set_error(SNN_ERR_INVALID, "bad arguments");
+    BCK(cudaStreamSynchronize(b->stream));
+    unsigned long long c[2];
+    BCK(cudaMemcpy(c, b->d_ic + 2 * k, sizeof(c), cudaMemcpyDeviceToHost));
+    if (step) *step = b->step;
+    if (spikes) *spikes = c[0];
+    if (events) *events = c[1];
+    return SNN_OK;
+}
+
+int snn_batch_get_info(snn_batch* b, int32_t k, snn_batch_info* info) {
+    if (!b || !info || k < 0 || k >= b->n_inst) return set_error(SNN_ERR_INVALID, "bad arguments");
+    info->n_instances = b->n_inst;
+    info->n_neurons_total = b->ntot;
+    info->n_neurons = b->cold_h[k].n;
+    info->n_synapses = (int64_t)b->nnz[k];
+    info->tiling = (int32_t)b->hot_h[k].key.z;
+    info->tune_us_warp = b->tune_us[0][k];
+    info->tune_us_block = b->tune_us[1][k];
+    info->blocks = b->blocks;
+    info->threads = kBThreads;
+    info->neurons_per_thread = b->npt;
+    info->graph = b->graph_ok ? 1 : 0;
+    info->graph_steps = kGraphChunk;
+    return SNN_OK;
+}
+
+int snn_batch_set_tiling(snn_batch* b, int32_t k, int32_t tiling) {
+    if (!b || k < 0 || k >= b->n_inst || (tiling != 0 && tiling != 1))
+        return set_error(SNN_ERR_INVALID, "bad arguments");
+    b->hot_h[k].key.z = (uint32_t)tiling;
+    BCK(cudaMemcpyAsync(b->d_hot + k, &b->hot_h[k], sizeof(InstHot), cudaMemcpyHostToDevice,
+                        b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return SNN_OK;
+}
+
+int snn_batch_destroy(snn_batch* b) {
+    if (!b) return SNN_OK;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    return SNN_OK;
+}
+
+}  // extern "C"

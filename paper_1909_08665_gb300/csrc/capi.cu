@@ -377,7 +377,8 @@ int finish_network(snn_net* net) {
     return SNN_OK;
 }
 
-int build_generated(snn_net* net) {
+// the synaptic rows (row starts, words, per-partition segment offsets)
+int build_rows(snn_net* net) {
     cudaStream_t s = net->stream;
     const int n = net->n, P = net->P;
     CALL(dalloc(&net->d_part_lo, P + 1, "partitions"));
@@ -415,6 +416,11 @@ int build_generated(snn_net* net) {
     CALL(dalloc(&net->d_seg, (size_t)n * (P + 1) + 4, "row segments"));
     CK(launch_build_fill(bp, net->d_row_start, net->d_words, net->d_seg, s));
     CK(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+int build_generated(snn_net* net) {
+    CALL(build_rows(net));
     return finish_network(net);
 }
 
@@ -481,6 +487,57 @@ int host_step_constants(const snn_config* cfg, float prop[4], float cdc[kMaxPop]
     *wext_q = tmp.wext_q;
     *n_ref = tmp.n_ref;
     return SNN_OK;
+}
+
+int host_tables(const snn_config* cfg, HostTables* out) {
+    CALL(validate(cfg));
+    static thread_local snn_net tmp;
+    tmp.cfg = *cfg;
+    CALL(make_tables(&tmp));
+    out->n_pop = cfg->n_pop;
+    out->pop_start[0] = 0;
+    for (int p = 0; p < kMaxPop; ++p)
+        out->pop_start[p + 1] = out->pop_start[p] + (p < cfg->n_pop ? cfg->pop_size[p] : 0);
+    out->n = out->pop_start[cfg->n_pop];
+    std::memcpy(out->wtab, tmp.wtab, sizeof(out->wtab));
+    for (int p = 0; p < kMaxPop; ++p)
+        for (int m = 0; m < kPoisTable; ++m) out->pois[p][m] = tmp.pois[p][m];
+    for (int k = 0; k < 4; ++k) out->prop[k] = tmp.prop[k];
+    for (int p = 0; p < kMaxPop; ++p) out->cdc[p] = tmp.cdc[p];
+    out->theta = (float)cfg->theta;
+    out->wext_q = tmp.wext_q;
+    out->n_ref = tmp.n_ref;
+    out->mode = cfg->input_mode;
+    return SNN_OK;
+}
+
+int build_rows_device(const snn_config* cfg, uint64_t seed, cudaStream_t stream,
+                      unsigned long long** row_start, uint32_t** words, uint64_t* nnz) {
+    CALL(validate(cfg));
+    snn_net* net = new snn_net();
+    net->cfg = *cfg;
+    net->seed = seed;
+    net->stream = stream;
+    net->n_pop = cfg->n_pop;
+    net->pop_start[0] = 0;
+    for (int p = 0; p < kMaxPop; ++p)
+        net->pop_start[p + 1] = net->pop_start[p] + (p < cfg->n_pop ? cfg->pop_size[p] : 0);
+    net->n = net->pop_start[cfg->n_pop];
+    int rc = make_tables(net);
+    if (rc == SNN_OK) {
+        net->P = 1;                                  // whole rows: one partition
+        net->part_lo = {0, net->n};
+        rc = build_rows(net);
+    }
+    if (rc == SNN_OK) {
+        *row_start = net->d_row_start;
+        *words = net->d_words;
+        *nnz = net->nnz;
+        net->d_row_start = nullptr;
+        net->d_words = nullptr;
+    }
+    free_net(net);
+    return rc;
 }
 
 int set_error(int code, const char* msg) { return fail(code, msg); }

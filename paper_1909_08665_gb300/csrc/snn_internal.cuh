@@ -90,6 +90,18 @@ struct SlotPops {
     int32_t pop_start[kMaxPop + 1];
 };
 
+// model constants and tables of one configuration, computed on the host
+struct HostTables {
+    int32_t n, n_pop;
+    int32_t pop_start[kMaxPop + 1];
+    int32_t wtab[kMaxPop * kMaxPop * kWCodes];
+    uint64_t pois[kMaxPop][kPoisTable];
+    float prop[4];                      // P22, P21, P11, P20
+    float cdc[kMaxPop];
+    float theta;
+    int32_t wext_q, n_ref, mode;
+};
+
 struct StepParams {
     int32_t n, n_pop, n_part, ncmax;
     int32_t pop_start[kMaxPop + 1];

@@ -1,0 +1,117 @@
+"""Parity at the benchmark's full size (77,169 neurons, ~3e8 synapses) and in
+the launch configuration the benchmark times, plus the statistical comparison
+the paper uses between simulators (Sec. 4.2).
+
+The oracle builds the full network itself (all host cores); spike rasters and
+fp32 state are compared bit for bit over 100 steps, and single rows of the
+network are compared against the oracle's stand-alone row generator.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_1909_08665_gb300 as pkg  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def full():
+    cfg = workload.microcircuit(1.0)
+    net = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
+    return cfg, net
+
+
+def test_full_size_sampled_rows(full):
+    cfg, net = full
+    rp, wd, _ = net.export_network()
+    assert abs(rp[-1] / 3.0e8 - 1.0) < 0.01           # ~0.3 billion synapses (Sec. 2.1)
+    rng = np.random.default_rng(0)
+    for j in np.r_[0, net.n - 1, rng.integers(0, net.n, 6)]:
+        tg, dl, wc = oracle.network_row(cfg, cfg["seed"], int(j))
+        np.testing.assert_array_equal(wd[rp[j]:rp[j + 1]], pkg.encode_words(tg, dl, wc))
+
+
+def test_full_size_raster_bit_exact_100_steps(full):
+    cfg, _ = full
+    net = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
+    info = net.info()
+    assert info["n_part"] >= 100 and info["ring_in_shared"] == 1    # the benchmark's launch shape
+    onet = oracle.Network(cfg, n_threads=os.cpu_count())
+    sim = oracle.Simulation(onet)
+    steps = 100
+    net.step(steps)
+    net.sync()
+    sim.run(steps)
+    g = net.read_spikes()
+    o = sim.raster()
+    assert o[0].size > 1000
+    np.testing.assert_array_equal(g[0], o[0])
+    np.testing.assert_array_equal(g[1], o[1])
+    g_u, g_i, g_r = net.state()
+    o_u, o_i, o_r, o_ring = sim.state()
+    np.testing.assert_array_equal(g_u.view(np.uint32), o_u.view(np.uint32))
+    np.testing.assert_array_equal(g_i.view(np.uint32), o_i.view(np.uint32))
+    np.testing.assert_array_equal(g_r, o_r)
+    np.testing.assert_array_equal(net.ring(), o_ring.astype(np.int32))
+    assert net.counters()["events"] == sim.counters()["events"]
+
+
+def test_full_size_delivery_both_tilings(full):
+    cfg, net = full
+    onet = oracle.Network(cfg, n_threads=os.cpu_count())
+    for tiling in (0, 1):
+        fresh = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
+        spikes = workload.random_spike_list(fresh.n, 4000, seed=11 + tiling)
+        d = torch.from_numpy(spikes.astype(np.int32)).cuda()
+        fresh.deliver(d.data_ptr(), spikes.size, 777, tiling)
+        fresh.sync()
+        ref = onet.deliver(spikes.astype(np.int32), 777)
+        np.testing.assert_array_equal(fresh.ring(), ref.astype(np.int32))
+        fresh.close()
+
+
+def _stats(cfg, st, ids, t0, t1):
+    rates = oracle.population_rates(cfg, st, ids, t0, t1)
+    n = int(sum(cfg["pop_sizes"]))
+    cv = oracle.cv_isi(st, ids, n, t0, t1)
+    bounds = np.cumsum([0] + list(cfg["pop_sizes"]))
+    cv_pop = np.array([np.nanmean(cv[bounds[p]:bounds[p + 1]]) for p in range(8)])
+    cc_pop = []
+    for p in range(8):
+        ids_p = np.arange(bounds[p], min(bounds[p] + 200, bounds[p + 1]))
+        cc = oracle.binned_correlations(st, ids, ids_p, t0, t1, 20)
+        cc_pop.append(np.nanmean(cc) if cc.size else 0.0)
+    return rates, cv_pop, np.array(cc_pop)
+
+
+def test_statistics_agree_across_seeds():
+    """Past the divergence horizon the comparison is statistical (Sec. 4.2):
+    the GPU run with one seed against oracle runs with other seeds; the GPU's
+    per-population rate, CV of ISI and correlation must fall within the
+    oracle's own seed-to-seed spread."""
+    steps, t0 = 6000, 1000
+    g_cfg = workload.microcircuit(0.1, seed=101)
+    net = pkg.Microcircuit(g_cfg, stream=torch.cuda.current_stream())
+    net.step(steps)
+    st, ids = net.read_spikes()
+    g = _stats(g_cfg, st, ids, t0, steps)
+    refs = []
+    for seed in (202, 303, 404, 505):
+        cfg = workload.microcircuit(0.1, seed=seed)
+        sim = oracle.Simulation(oracle.Network(cfg))
+        sim.run(steps)
+        refs.append(_stats(cfg, *sim.raster(), t0, steps))
+    for k, name in enumerate(["rate", "cv", "corr"]):
+        ref = np.array([r[k] for r in refs])
+        mean, sd = ref.mean(axis=0), ref.std(axis=0, ddof=1)
+        tol = np.maximum(4.0 * sd, 0.15 * np.abs(mean) + 0.02)
+        assert np.all(np.abs(g[k] - mean) <= tol), (name, g[k], mean, tol)
