@@ -151,6 +151,19 @@ def lib():
         L.orc_sim_counters.argtypes = [C.c_void_p, P(C.c_int64), P(C.c_int64), P(C.c_int64),
                                        P(C.c_int32)]
         L.orc_sim_free.argtypes = [C.c_void_p]
+        L.orc_sim_run_trace.argtypes = [C.c_void_p, C.c_int64, P(C.c_float), P(C.c_uint8),
+                                        P(C.c_int32)]
+        L.orc_sim_run_trace.restype = C.c_int64
+        L.orc_grad_backward.argtypes = [C.c_void_p, P(OrcConfig), C.c_int, C.c_int64,
+                                        P(C.c_double), P(C.c_double), P(C.c_uint8),
+                                        P(C.c_double), P(C.c_double), P(C.c_double),
+                                        P(C.c_double)]
+        L.orc_relaxed_forward.argtypes = [C.c_void_p, P(OrcConfig), C.c_int64, P(C.c_double),
+                                          P(C.c_double), P(C.c_double), P(C.c_double),
+                                          P(C.c_double)]
+        L.orc_surrogate_forward.argtypes = [C.c_void_p, P(OrcConfig), P(C.c_double), C.c_double,
+                                            C.c_int64, P(C.c_double), P(C.c_float),
+                                            P(C.c_uint8), P(C.c_int32), P(C.c_double)]
         _lib = L
     return _lib
 
@@ -338,6 +351,17 @@ class Simulation:
         lib().orc_sim_set_state(self._h, _ptr(u, C.c_float), _ptr(i_syn, C.c_float),
                                 _ptr(refr, C.c_int32), _ptr(ring, C.c_int64), int(step))
 
+    def run_trace(self, n_steps: int):
+        """Run ``n_steps`` recording, per step and neuron, u after the
+        membrane update (before reset), flags = spike | non-refractory << 1,
+        and the Poisson count."""
+        u = np.zeros((n_steps, self.n), np.float32)
+        f = np.zeros((n_steps, self.n), np.uint8)
+        k = np.zeros((n_steps, self.n), np.int32)
+        lib().orc_sim_run_trace(self._h, int(n_steps), _ptr(u, C.c_float), _ptr(f, C.c_uint8),
+                                _ptr(k, C.c_int32))
+        return u, f, k
+
     def counters(self):
         a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32()
         lib().orc_sim_counters(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d))
@@ -348,6 +372,119 @@ class Simulation:
         if getattr(self, "_h", None):
             lib().orc_sim_free(self._h)
             self._h = None
+
+
+# --------------------------------------------------------------------------
+# gradient of a population-rate loss (surrogate BPTT; the paper has none)
+# --------------------------------------------------------------------------
+HARD, RELAXED = 0, 1
+
+
+def with_params(cfg: dict, alpha, nu: float) -> dict:
+    """Configuration with projection weight scales ``alpha`` [8][8] (target,
+    source) and background rate ``nu`` (Hz)."""
+    import copy
+    c = copy.deepcopy(cfg)
+    a = np.asarray(alpha, np.float64).reshape(MAX_POP, MAX_POP)
+    npop = len(c["pop_sizes"])
+    c["proj_scale"] = [[float(a[p][q]) for q in range(npop)] for p in range(npop)]
+    c["nu_bg"] = float(nu)
+    return c
+
+
+def rate_loss(rates, targets) -> float:
+    """Mean squared error of the population rates (Hz^2)."""
+    d = np.asarray(rates, np.float64) - np.asarray(targets, np.float64)
+    return float(np.mean(d * d))
+
+
+def rate_loss_grad(rates, targets) -> np.ndarray:
+    d = np.asarray(rates, np.float64) - np.asarray(targets, np.float64)
+    return 2.0 * d / d.size
+
+
+def rates_from_flags(cfg: dict, flags: np.ndarray) -> np.ndarray:
+    """Population rates (Hz) of a recorded run: spikes / (N_p T)."""
+    bounds = np.cumsum([0] + list(cfg["pop_sizes"]))
+    spk = (flags & 1).sum(axis=0, dtype=np.int64)
+    T = flags.shape[0] * cfg["dt"] * 1e-3
+    return np.array([spk[bounds[p]:bounds[p + 1]].sum() / (cfg["pop_sizes"][p] * T)
+                     for p in range(len(cfg["pop_sizes"]))], np.float64)
+
+
+def _g8(g_rate):
+    g = np.zeros(MAX_POP, np.float64)
+    g[:len(g_rate)] = g_rate
+    return g
+
+
+def grad_backward(net: Network, cfg: dict, mode: int, u_tr, s_tr, m_tr, g_rate, z=None):
+    """Adjoint pass of the hard (mode 0) or relaxed (mode 1) model over the
+    recorded trajectory; returns (dL/dalpha [8][8], dL/dnu)."""
+    c = make_config(cfg)
+    u = np.ascontiguousarray(u_tr, np.float64)
+    sv = np.ascontiguousarray(s_tr, np.float64)
+    m = np.ascontiguousarray(m_tr if m_tr is not None else np.zeros(u.shape, np.uint8), np.uint8)
+    zz = np.ascontiguousarray(z if z is not None else np.zeros(u.shape), np.float64)
+    g = _g8(g_rate)
+    ga = np.zeros(MAX_POP * MAX_POP, np.float64)
+    gn = C.c_double()
+    lib().orc_grad_backward(net._h, C.byref(c), int(mode), int(u.shape[0]), _ptr(u, C.c_double),
+                            _ptr(sv, C.c_double), _ptr(m, C.c_uint8), _ptr(zz, C.c_double),
+                            _ptr(g, C.c_double), _ptr(ga, C.c_double), C.byref(gn))
+    return ga.reshape(MAX_POP, MAX_POP), gn.value
+
+
+def relaxed_forward(net: Network, cfg: dict, n_steps: int, u0, z, record: bool = False):
+    """Sigmoid-relaxed model in double; returns rates (and the u, s records)."""
+    c = make_config(cfg)
+    n = net.n
+    u0 = np.ascontiguousarray(u0, np.float64)
+    zz = np.ascontiguousarray(z, np.float64)
+    rates = np.zeros(MAX_POP, np.float64)
+    ut = np.zeros((n_steps, n)) if record else None
+    st = np.zeros((n_steps, n)) if record else None
+    lib().orc_relaxed_forward(net._h, C.byref(c), int(n_steps), _ptr(u0, C.c_double),
+                              _ptr(zz, C.c_double),
+                              _ptr(ut, C.c_double) if record else None,
+                              _ptr(st, C.c_double) if record else None,
+                              _ptr(rates, C.c_double))
+    npop = len(cfg["pop_sizes"])
+    return (rates[:npop], ut, st) if record else rates[:npop]
+
+
+def surrogate_forward(net0: Network, cfg0: dict, alpha, nu: float, n_steps: int, u0,
+                      u_star, f_star, k_star) -> np.ndarray:
+    """Smooth model around a recorded hard run (its exact gradient at the
+    recording's parameters is the surrogate gradient); returns rates."""
+    c = make_config(cfg0)
+    a = np.ascontiguousarray(np.asarray(alpha, np.float64).reshape(-1), np.float64)
+    u0 = np.ascontiguousarray(u0, np.float64)
+    us = np.ascontiguousarray(u_star, np.float32)
+    fs = np.ascontiguousarray(f_star, np.uint8)
+    ks = np.ascontiguousarray(k_star, np.int32)
+    rates = np.zeros(MAX_POP, np.float64)
+    lib().orc_surrogate_forward(net0._h, C.byref(c), _ptr(a, C.c_double), float(nu),
+                                int(n_steps), _ptr(u0, C.c_double), _ptr(us, C.c_float),
+                                _ptr(fs, C.c_uint8), _ptr(ks, C.c_int32), _ptr(rates, C.c_double))
+    return rates[:len(cfg0["pop_sizes"])]
+
+
+def hard_gradient(cfg: dict, alpha, nu: float, n_steps: int, targets, seed: int | None = None,
+                  n_threads: int | None = None):
+    """Hard-model forward at (alpha, nu) with the recorded trajectory, then the
+    surrogate backward of the rate MSE.  Returns a dict with rates, loss,
+    g_alpha [8][8], g_nu and the trajectory (u0, u, flags, k, network)."""
+    cp = with_params(cfg, alpha, nu)
+    net = Network(cp, seed=seed, n_threads=n_threads or os.cpu_count())
+    sim = Simulation(net, seed=seed)
+    u0 = sim.state()[0].copy()
+    u, f, k = sim.run_trace(n_steps)
+    rates = rates_from_flags(cp, f)
+    g_rate = rate_loss_grad(rates, targets)
+    ga, gn = grad_backward(net, cp, HARD, u, (f & 1).astype(np.float64), f, g_rate)
+    return {"rates": rates, "loss": rate_loss(rates, targets), "g_alpha": ga, "g_nu": gn,
+            "u0": u0, "u": u, "flags": f, "k": k, "net": net, "cfg": cp}
 
 
 # --------------------------------------------------------------------------

@@ -431,6 +431,9 @@ struct orc_sim {
     int64_t* rs_step;
     int32_t* rs_id;
     int64_t rs_n, rs_cap;
+    float* tr_u;            /* optional per-step trace (gradient runs) */
+    uint8_t* tr_f;
+    int32_t* tr_k;
 };
 
 orc_sim* orc_sim_create(const orc_net* net, const orc_config* c, uint64_t seed, const float* u0)
@@ -504,6 +507,7 @@ static void sim_step(orc_sim* s)
     uint32_t out[4];
     for (int64_t i = 0; i < n; ++i) {
         int p = pop_of(net->pop_start, net->n_pop, i);
+        int k = 0, updated = 0;
         /* 1. input for this step from the neuron's ring buffer; clear slot */
         int64_t acc = s->ring[slot * n + i];
         s->ring[slot * n + i] = 0;
@@ -511,7 +515,7 @@ static void sim_step(orc_sim* s)
         if (s->mode == 0) {
             uint32_t ctr[4] = {(uint32_t)i, (uint32_t)(t >> 2), 3u, (uint32_t)(t >> 34)};
             orc_philox4x32_10(ctr, s->key, out);
-            int k = orc_poisson_count(out[t & 3], s->pois + p * ORC_POIS_TABLE);
+            k = orc_poisson_count(out[t & 3], s->pois + p * ORC_POIS_TABLE);
             acc += (int64_t)k * (int64_t)s->wext_q;
         }
         if (acc > 2147483647LL || acc < -2147483648LL) s->saturated = 1;
@@ -526,6 +530,12 @@ static void sim_step(orc_sim* s)
             float v = a + b;
             if (s->mode == 1) v = v + s->cdc[p];
             s->u[i] = v;
+            updated = 1;
+        }
+        if (s->tr_u) {
+            s->tr_u[i] = s->u[i];
+            s->tr_f[i] = (uint8_t)(updated << 1);
+            s->tr_k[i] = k;
         }
         /* 4. synaptic current: decay, then this step's input (1/256 pA units) */
         float decay = s->P11 * s->i_syn[i];
@@ -537,7 +547,13 @@ static void sim_step(orc_sim* s)
             s->refr[i] = s->n_ref;
             s->spk[n_spk++] = (int32_t)i;
             raster_push(s, t, (int32_t)i);
+            if (s->tr_f) s->tr_f[i] |= 1u;
         }
+    }
+    if (s->tr_u) {
+        s->tr_u += n;
+        s->tr_f += n;
+        s->tr_k += n;
     }
     /* 6. deliver every spike through its row into the ring slots t + d */
     for (int64_t k = 0; k < n_spk; ++k) {
@@ -583,6 +599,22 @@ int64_t orc_sim_run(orc_sim* s, int64_t n_steps)
     return s->rs_n - before;
 }
 
+/* orc_sim_run with a record of every step: u_trace[t][i] = u after the
+ * membrane update of step t (before reset), flags[t][i] = spike (bit 0) |
+ * non-refractory update (bit 1), kbg[t][i] = Poisson count of step t. */
+int64_t orc_sim_run_trace(orc_sim* s, int64_t n_steps, float* u_trace, uint8_t* flags,
+                          int32_t* kbg)
+{
+    s->tr_u = u_trace;
+    s->tr_f = flags;
+    s->tr_k = kbg;
+    int64_t r = orc_sim_run(s, n_steps);
+    s->tr_u = NULL;
+    s->tr_f = NULL;
+    s->tr_k = NULL;
+    return r;
+}
+
 int64_t orc_sim_raster_count(const orc_sim* s) { return s->rs_n; }
 
 void orc_sim_raster_read(orc_sim* s, int64_t* steps, int32_t* ids)
@@ -625,4 +657,287 @@ void orc_sim_free(orc_sim* s)
     free(s->u); free(s->i_syn); free(s->refr); free(s->ring); free(s->spk);
     free(s->rs_step); free(s->rs_id);
     free(s);
+}
+
+/* ======================================================================== */
+/* Gradient of a population-rate loss with respect to the 64 projection      */
+/* weight scales alpha_pq (cfg.proj_scale) and the background rate nu        */
+/* (cfg.nu_bg).  The paper has no gradient; this is the differentiable form  */
+/* of its benchmark network (Sec. 2.1, Eq. 1), by backpropagation through    */
+/* time on the same step grid.  Rates r_p = (spikes of pop p) / (N_p T).     */
+/*                                                                          */
+/* Two models share one adjoint routine (orc_grad_backward):                */
+/*  mode 0, hard model with surrogate derivative: the forward is the        */
+/*    simulation above; d s / d u := 1 / (1 + 10 |u - theta|)^2 (fast        */
+/*    sigmoid, slope 10 per mV); reset and refractory are treated as          */
+/*    constants (u_after = u (1 - s) with s held fixed; steps clamped by the   */
+/*    refractory counter pass no gradient); the fixed-point rounding of the   */
+/*    weights and the Poisson count are passed straight through:              */
+/*    d w / d alpha_pq = w_base, d k / d nu = K_ext dt.                       */
+/*  mode 1, sigmoid-relaxed model in double: s = 1/(1 + exp(-10 (u-theta))),  */
+/*    soft reset u_after = u (1 - s), no refractory period, unrounded          */
+/*    weights alpha_pq w_base, background (lambda + sqrt(lambda) z) w_ext     */
+/*    with fixed normal draws z; its gradient is exact.                        */
+/*                                                                          */
+/* Pins: mode 1 against central finite differences of orc_relaxed_forward;  */
+/* mode 0 against central finite differences of orc_surrogate_forward, a     */
+/* smooth model whose exact gradient at the expansion point is the surrogate */
+/* gradient (spikes s* + F(u - theta) - F(u* - theta), F(x) = x/(1+10|x|),    */
+/* around a recorded hard trajectory u*, s*).                                 */
+/* ======================================================================== */
+
+static double fast_sigmoid_slope(double x) { double a = 1.0 + 10.0 * fabs(x); return 1.0 / (a * a); }
+static double fast_sigmoid(double x) { return x / (1.0 + 10.0 * fabs(x)); }
+static double logistic10(double x) { return 1.0 / (1.0 + exp(-10.0 * x)); }
+
+/* unrounded base weight of code k of projection q -> p, in pA */
+static double base_weight(const orc_config* c, int p, int q, int k)
+{
+    double z = orc_norm_quantile(((double)k + 0.5) / (double)ORC_WCODES);
+    return (c->w_mean[p][q] + c->w_sd[p][q] * z) * c->w_scale;
+}
+
+static void base_table(const orc_config* c, double* wb)
+{
+    for (int p = 0; p < ORC_MAX_POP; ++p)
+        for (int q = 0; q < ORC_MAX_POP; ++q)
+            for (int k = 0; k < ORC_WCODES; ++k)
+                wb[(p * ORC_MAX_POP + q) * ORC_WCODES + k] =
+                    (p < c->n_pop && q < c->n_pop) ? base_weight(c, p, q, k) : 0.0;
+}
+
+/* d L / d s_{j,t} of the rate loss: g_rate[p] / (N_p T_seconds) */
+static void spike_loss_weights(const orc_config* c, int64_t n_steps, const double* g_rate,
+                               double* gs)
+{
+    double T = (double)n_steps * c->dt / 1000.0;
+    for (int p = 0; p < ORC_MAX_POP; ++p)
+        gs[p] = (p < c->n_pop && c->pop_size[p] > 0) ? g_rate[p] / ((double)c->pop_size[p] * T) : 0.0;
+}
+
+/*
+ * Adjoint pass, from the last step back to the first.  With lu_t = dL/du_t
+ * (u after the update of step t, before reset), lI_t = dL/dI_t, m_t = 1 when
+ * step t took the non-refractory update:
+ *   ds_{j,t} = dL/ds_{j,t} = gs[p(j)] + sum over row j of  W * lI_{i,t+d}
+ *   lu_t     = ds_t * s'(u_t) + R_t * lubar_t,  lubar_t = m_{t+1} P22 lu_{t+1}
+ *   lI_t     = P11 lI_{t+1} + m_{t+1} P21 lu_{t+1}
+ * (R_t = 1 - s_t for the detached reset, (1 - s) - u s' for the soft reset),
+ *   dL/dalpha_pq += s_{j,t} w_base(p,q,code) lI_{i,t+d}   (words of j into p)
+ *   dL/dnu       += lI_{i,t} d x_{i,t} / d nu.
+ * u_tr, s_tr: [n_steps][n]; m_tr: [n_steps][n] (ignored in mode 1, where
+ * every step updates); z: [n_steps][n] (mode 1 only).
+ */
+int orc_grad_backward(const orc_net* net, const orc_config* c, int mode, int64_t n_steps,
+                      const double* u_tr, const double* s_tr, const uint8_t* m_tr,
+                      const double* z, const double* g_rate, double* g_alpha, double* g_nu)
+{
+    const int64_t n = net->n;
+    const int D = c->ring_depth;
+    double pd[4];
+    float pf[4];
+    orc_propagators(c, pd, pf);
+    const double P22 = mode == 0 ? (double)pf[0] : pd[0];
+    const double P21 = mode == 0 ? (double)pf[1] : pd[1];
+    const double P11 = mode == 0 ? (double)pf[2] : pd[2];
+    const double theta = mode == 0 ? (double)(float)c->theta : c->theta;
+    double* wb = (double*)malloc(sizeof(double) * ORC_MAX_POP * ORC_MAX_POP * ORC_WCODES);
+    double* weff = (double*)malloc(sizeof(double) * ORC_MAX_POP * ORC_MAX_POP * ORC_WCODES);
+    base_table(c, wb);
+    for (int p = 0; p < ORC_MAX_POP; ++p)
+        for (int q = 0; q < ORC_MAX_POP; ++q)
+            for (int k = 0; k < ORC_WCODES; ++k) {
+                int idx = (p * ORC_MAX_POP + q) * ORC_WCODES + k;
+                weff[idx] = mode == 0 ? (double)net->wtab[idx] / 256.0 : c->proj_scale[p][q] * wb[idx];
+            }
+    double gs[ORC_MAX_POP];
+    spike_loss_weights(c, n_steps, g_rate, gs);
+    /* d x / d nu per population (mode 0) or its z-free part (mode 1) */
+    const double dts = c->dt / 1000.0;
+    double wq = mode == 0 ? (double)llround(c->w_ext * 256.0) / 256.0 : c->w_ext;
+    double dnu[ORC_MAX_POP], lam[ORC_MAX_POP];
+    for (int p = 0; p < ORC_MAX_POP; ++p) {
+        dnu[p] = (p < c->n_pop && c->input_mode == 0) ? wq * c->k_ext[p] * dts : 0.0;
+        lam[p] = (p < c->n_pop) ? c->nu_bg * c->k_ext[p] * dts : 0.0;
+    }
+    double* lu = (double*)calloc((size_t)n, sizeof(double));
+    double* lI = (double*)calloc((size_t)n, sizeof(double));
+    uint8_t* mnext = (uint8_t*)calloc((size_t)n, 1);
+    double* lIr = (double*)calloc((size_t)D * (size_t)n, sizeof(double));
+    double* ds = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double ga[ORC_MAX_POP * ORC_MAX_POP] = {0};
+    double gnu = 0.0;
+    for (int64_t t = n_steps - 1; t >= 0; --t) {
+        const double* ut = u_tr + t * n;
+        const double* st = s_tr + t * n;
+        /* spikes: loss term plus everything they feed through the rows */
+        for (int64_t j = 0; j < n; ++j) {
+            int q = pop_of(net->pop_start, net->n_pop, j);
+            double acc = gs[q];
+            for (int64_t e = net->row_ptr[j]; e < net->row_ptr[j + 1]; ++e) {
+                int64_t i = net->tgt[e];
+                int p = pop_of(net->pop_start, net->n_pop, i);
+                int idx = (p * ORC_MAX_POP + q) * ORC_WCODES + net->wcode[e];
+                double l = lIr[((t + net->delay[e]) % D) * n + i];
+                acc += weff[idx] * l;
+                if (st[j] != 0.0) ga[p * ORC_MAX_POP + q] += st[j] * wb[idx] * l;
+            }
+            ds[j] = acc;
+        }
+        /* membrane and current adjoints of step t */
+        for (int64_t i = 0; i < n; ++i) {
+            int p = pop_of(net->pop_start, net->n_pop, i);
+            double lub = mnext[i] ? P22 * lu[i] : 0.0;
+            double lIt = P11 * lI[i] + (mnext[i] ? P21 * lu[i] : 0.0);
+            double x = ut[i] - theta, s = st[i], lut;
+            if (mode == 0) {
+                lut = ds[i] * fast_sigmoid_slope(x) + (1.0 - s) * lub;
+            } else {
+                double sp = 10.0 * s * (1.0 - s);
+                lut = ds[i] * sp + ((1.0 - s) - ut[i] * sp) * lub;
+            }
+            lu[i] = lut;
+            lI[i] = lIt;
+            mnext[i] = mode == 0 ? (uint8_t)((m_tr[t * n + i] >> 1) & 1u) : 1u;
+            lIr[(t % D) * n + i] = lIt;
+            double dx = dnu[p];
+            if (mode == 1 && lam[p] > 0.0) dx *= 1.0 + z[t * n + i] / (2.0 * sqrt(lam[p]));
+            gnu += lIt * dx;
+        }
+    }
+    for (int k = 0; k < ORC_MAX_POP * ORC_MAX_POP; ++k) g_alpha[k] = ga[k];
+    *g_nu = gnu;
+    free(wb); free(weff); free(lu); free(lI); free(mnext); free(lIr); free(ds);
+    return 0;
+}
+
+/* Sigmoid-relaxed model (mode 1 above), forward in double.  u0: initial
+ * potentials; z: [n_steps][n] normal draws; u_tr, s_tr may be NULL. */
+int orc_relaxed_forward(const orc_net* net, const orc_config* c, int64_t n_steps,
+                        const double* u0, const double* z, double* u_tr, double* s_tr,
+                        double* rates)
+{
+    const int64_t n = net->n;
+    const int D = c->ring_depth;
+    double pd[4];
+    float pf[4];
+    orc_propagators(c, pd, pf);
+    double* wb = (double*)malloc(sizeof(double) * ORC_MAX_POP * ORC_MAX_POP * ORC_WCODES);
+    base_table(c, wb);
+    const double dts = c->dt / 1000.0;
+    double lam[ORC_MAX_POP];
+    for (int p = 0; p < ORC_MAX_POP; ++p) lam[p] = (p < c->n_pop) ? c->nu_bg * c->k_ext[p] * dts : 0.0;
+    double* u = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* I = (double*)calloc((size_t)n, sizeof(double));
+    double* s = (double*)calloc((size_t)n, sizeof(double));
+    double* ring = (double*)calloc((size_t)D * (size_t)n, sizeof(double));
+    double cnt[ORC_MAX_POP] = {0};
+    memcpy(u, u0, sizeof(double) * (size_t)n);
+    for (int64_t t = 0; t < n_steps; ++t) {
+        for (int64_t i = 0; i < n; ++i) {
+            int p = pop_of(net->pop_start, net->n_pop, i);
+            double x = ring[(t % D) * n + i];
+            ring[(t % D) * n + i] = 0.0;
+            if (c->input_mode == 0 && lam[p] > 0.0)
+                x += (lam[p] + sqrt(lam[p]) * z[t * n + i]) * c->w_ext;
+            double v = pd[0] * u[i] + pd[1] * I[i];
+            if (c->input_mode == 1) v += pd[3] * c->i_dc[p];
+            I[i] = pd[2] * I[i] + x;
+            double si = logistic10(v - c->theta);
+            if (u_tr) u_tr[t * n + i] = v;
+            if (s_tr) s_tr[t * n + i] = si;
+            s[i] = si;
+            u[i] = v * (1.0 - si);
+            cnt[p] += si;
+        }
+        for (int64_t j = 0; j < n; ++j) {
+            int q = pop_of(net->pop_start, net->n_pop, j);
+            for (int64_t e = net->row_ptr[j]; e < net->row_ptr[j + 1]; ++e) {
+                int64_t i = net->tgt[e];
+                int p = pop_of(net->pop_start, net->n_pop, i);
+                int idx = (p * ORC_MAX_POP + q) * ORC_WCODES + net->wcode[e];
+                ring[((t + net->delay[e]) % D) * n + i] += s[j] * c->proj_scale[p][q] * wb[idx];
+            }
+        }
+    }
+    double T = (double)n_steps * c->dt / 1000.0;
+    for (int p = 0; p < ORC_MAX_POP; ++p)
+        rates[p] = (p < c->n_pop && c->pop_size[p] > 0) ? cnt[p] / ((double)c->pop_size[p] * T) : 0.0;
+    free(wb); free(u); free(I); free(s); free(ring);
+    return 0;
+}
+
+/* Smooth model around a recorded hard trajectory (u*, s*, m*, k*) of the
+ * network net0 at parameters c0, written as deviations from that trajectory:
+ *   du_t = m*_t (P22 dubar_{t-1} + P21 dI_{t-1}),  dubar_t = du_t (1 - s*_t)
+ *   dI_t = P11 dI_{t-1} + dx_t
+ *   s_t  = s*_t + F(u*_t + du_t - theta) - F(u*_t - theta),  F(x) = x/(1+10|x|)
+ *   dx_t = sum over rows of  (s - s*)_{j,t-d} W_c + s*_{j,t-d} (alpha - alpha0) w_base
+ *          + (nu - nu0) K_ext dt w_ext,        W = wtab0/256 + (alpha - alpha0) w_base
+ * At (alpha0, nu0) every deviation is zero, so the model is the recorded hard
+ * run; its exact derivative there is the surrogate gradient of mode 0.
+ * u0 is unused (the deviations start at zero); kept for a uniform signature. */
+int orc_surrogate_forward(const orc_net* net0, const orc_config* c0, const double* alpha,
+                          double nu, int64_t n_steps, const double* u0, const float* u_star,
+                          const uint8_t* f_star, const int32_t* k_star, double* rates)
+{
+    (void)u0;
+    (void)k_star;
+    const int64_t n = net0->n;
+    const int D = c0->ring_depth;
+    double pd[4];
+    float pf[4];
+    orc_propagators(c0, pd, pf);
+    const double P22 = pf[0], P21 = pf[1], P11 = pf[2];
+    const double theta = (double)(float)c0->theta;
+    double* wb = (double*)malloc(sizeof(double) * ORC_MAX_POP * ORC_MAX_POP * ORC_WCODES);
+    double* w = (double*)malloc(sizeof(double) * ORC_MAX_POP * ORC_MAX_POP * ORC_WCODES);
+    double* dw = (double*)malloc(sizeof(double) * ORC_MAX_POP * ORC_MAX_POP * ORC_WCODES);
+    base_table(c0, wb);
+    for (int p = 0; p < ORC_MAX_POP; ++p)
+        for (int q = 0; q < ORC_MAX_POP; ++q)
+            for (int k = 0; k < ORC_WCODES; ++k) {
+                int idx = (p * ORC_MAX_POP + q) * ORC_WCODES + k;
+                dw[idx] = (alpha[p * ORC_MAX_POP + q] - c0->proj_scale[p][q]) * wb[idx];
+                w[idx] = (double)net0->wtab[idx] / 256.0 + dw[idx];
+            }
+    const double dts = c0->dt / 1000.0;
+    const double wq = (double)llround(c0->w_ext * 256.0) / 256.0;
+    double* du = (double*)calloc((size_t)n, sizeof(double));
+    double* dI = (double*)calloc((size_t)n, sizeof(double));
+    double* ds = (double*)calloc((size_t)n, sizeof(double));
+    double* ring = (double*)calloc((size_t)D * (size_t)n, sizeof(double));
+    double cnt[ORC_MAX_POP] = {0};
+    for (int64_t t = 0; t < n_steps; ++t) {
+        for (int64_t i = 0; i < n; ++i) {
+            int p = pop_of(net0->pop_start, net0->n_pop, i);
+            double dx = ring[(t % D) * n + i];
+            ring[(t % D) * n + i] = 0.0;
+            if (c0->input_mode == 0) dx += (nu - c0->nu_bg) * c0->k_ext[p] * dts * wq;
+            uint8_t f = f_star[t * n + i];
+            double dv = (f & 2u) ? P22 * du[i] + P21 * dI[i] : 0.0;
+            dI[i] = P11 * dI[i] + dx;
+            double sstar = (double)(f & 1u);
+            double us = (double)u_star[t * n + i] - theta;
+            ds[i] = fast_sigmoid(us + dv) - fast_sigmoid(us);
+            du[i] = dv * (1.0 - sstar);
+            cnt[p] += sstar + ds[i];
+        }
+        for (int64_t j = 0; j < n; ++j) {
+            double sstar = (double)(f_star[t * n + j] & 1u);
+            if (ds[j] == 0.0 && sstar == 0.0) continue;
+            int q = pop_of(net0->pop_start, net0->n_pop, j);
+            for (int64_t e = net0->row_ptr[j]; e < net0->row_ptr[j + 1]; ++e) {
+                int64_t i = net0->tgt[e];
+                int p = pop_of(net0->pop_start, net0->n_pop, i);
+                int idx = (p * ORC_MAX_POP + q) * ORC_WCODES + net0->wcode[e];
+                ring[((t + net0->delay[e]) % D) * n + i] += ds[j] * w[idx] + sstar * dw[idx];
+            }
+        }
+    }
+    double T = (double)n_steps * c0->dt / 1000.0;
+    for (int p = 0; p < ORC_MAX_POP; ++p)
+        rates[p] = (p < c0->n_pop && c0->pop_size[p] > 0) ? cnt[p] / ((double)c0->pop_size[p] * T) : 0.0;
+    free(wb); free(w); free(dw); free(du); free(dI); free(ds); free(ring);
+    return 0;
 }

@@ -78,5 +78,19 @@ void orc_sim_set_state(orc_sim* s, const float* u, const float* i_syn, const int
 void orc_sim_counters(const orc_sim* s, int64_t* step, int64_t* spikes, int64_t* events,
                       int32_t* saturated);
 void orc_sim_free(orc_sim* s);
+int64_t orc_sim_run_trace(orc_sim* s, int64_t n_steps, float* u_trace, uint8_t* flags,
+                          int32_t* kbg);
+
+/* gradient of a population-rate loss (hard model with surrogate, mode 0;
+ * sigmoid-relaxed model, mode 1) and the two smooth forwards that pin it */
+int orc_grad_backward(const orc_net* net, const orc_config* c, int mode, int64_t n_steps,
+                      const double* u_tr, const double* s_tr, const uint8_t* m_tr,
+                      const double* z, const double* g_rate, double* g_alpha, double* g_nu);
+int orc_relaxed_forward(const orc_net* net, const orc_config* c, int64_t n_steps,
+                        const double* u0, const double* z, double* u_tr, double* s_tr,
+                        double* rates);
+int orc_surrogate_forward(const orc_net* net0, const orc_config* c0, const double* alpha,
+                          double nu, int64_t n_steps, const double* u0, const float* u_star,
+                          const uint8_t* f_star, const int32_t* k_star, double* rates);
 
 #endif
