@@ -258,6 +258,52 @@ int snn_step_noalloc(const snn_config* cfg, uint64_t seed, const snn_noalloc_io*
 
 /*
  * ---------------------------------------------------------------------------
+ * State, parameters and gradient.
+ * ---------------------------------------------------------------------------
+ */
+
+/* snn_save_state -- serialise the dynamic state (u, I, refractory counters,
+ * ring buffers and the step counter; Sec. 3.1.2 ring buffers) into a host
+ * buffer: 32-byte header, then u[n] f32, I[n] f32, refr[n] i32 and
+ * ring[64][n] i32.  With buf_host == NULL only *n_bytes is set.  Synchronises.
+ * Errors: SNN_ERR_INVALID (cap smaller than *n_bytes). */
+int snn_save_state(snn_net* net, void* buf_host, int64_t cap, int64_t* n_bytes);
+
+/* snn_load_state -- restore a state saved from a network of the same size;
+ * later steps continue from it exactly (bit for bit).  Synchronises. */
+int snn_load_state(snn_net* net, const void* buf_host, int64_t n_bytes);
+
+/* snn_set_params -- set the 64 projection weight scales alpha[p*8 + q]
+ * (target p, source q; they multiply every weight of the projection before
+ * its fixed-point rounding) and the background rate nu_bg (Hz).  The
+ * connectivity, delays and weight codes are unchanged.  Synchronises.
+ * Errors: SNN_ERR_INVALID (non-finite scale, negative rate, weight outside
+ * the fixed-point range). */
+int snn_set_params(snn_net* net, const double* scales, double nu_bg);
+
+/*
+ * snn_grad_forward -- run n_steps from the current state as snn_step does,
+ * keeping a device checkpoint of the full state every ckpt_every steps, and
+ * return the population rates (Hz) over those steps in rates_host[8].
+ * snn_grad_backward -- given g_rate[8] = dL/d rate_p of any loss of those
+ * rates, return dL/d alpha (g_alpha[p*8 + q]) and dL/d nu_bg (*g_nu) by
+ * backpropagation through time: each segment is restored from its
+ * checkpoint, re-run with its trajectory recorded, and differentiated in
+ * reverse.  Spike derivative: the fast-sigmoid surrogate 1/(1+10|u-theta|)^2
+ * per mV; reset and refractory are held fixed; the weight rounding and the
+ * Poisson count pass their derivative straight through (d w/d alpha = the
+ * unrounded base weight, d k/d nu = K_ext dt).  fp32 adjoint state, double
+ * accumulation, deterministic.  The paper has no gradient: this is the
+ * differentiable form of its network (Sec. 2.1, Eq. 1).  The backward leaves
+ * the state, counters and raster as they were after the forward.
+ * Errors: SNN_ERR_INVALID (no forward, or the network was stepped since),
+ * SNN_ERR_OOM, SNN_ERR_TIMEOUT.
+ */
+int snn_grad_forward(snn_net* net, int64_t n_steps, int32_t ckpt_every, double* rates_host);
+int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, double* g_nu);
+
+/*
+ * ---------------------------------------------------------------------------
  * Batched instances.  The paper simulates one network at a time; a batch runs
  * many independent networks of the same model (Sec. 2.1, Eq. 1) -- each with
  * its own configuration (e.g. its own scale) and seed -- in ONE persistent

@@ -99,7 +99,9 @@ NOALLOC_MAX_NEURONS = 131072
 
 EXPORTED = ["snn_create", "snn_create_from_rows", "snn_step", "snn_sync", "snn_read_spikes",
             "snn_raster_size", "snn_read_state", "snn_read_ring", "snn_counters", "snn_get_info",
-            "snn_export_network", "snn_deliver", "snn_step_noalloc", "snn_batch_create",
+            "snn_export_network", "snn_deliver", "snn_step_noalloc", "snn_save_state",
+            "snn_load_state", "snn_set_params", "snn_grad_forward", "snn_grad_backward",
+            "snn_batch_create",
             "snn_batch_step", "snn_batch_sync", "snn_batch_read_spikes", "snn_batch_read_state",
             "snn_batch_counters", "snn_batch_get_info", "snn_batch_set_tiling",
             "snn_batch_destroy", "snn_destroy",
@@ -134,6 +136,11 @@ def lib():
         L.snn_deliver.argtypes = [vp, vp, C.c_int32, C.c_int64, C.c_int32]
         L.snn_step_noalloc.argtypes = [P(SnnConfig), C.c_uint64, P(SnnNoallocIO), C.c_int64,
                                        C.c_int64, vp]
+        L.snn_save_state.argtypes = [vp, vp, C.c_int64, P(C.c_int64)]
+        L.snn_load_state.argtypes = [vp, vp, C.c_int64]
+        L.snn_set_params.argtypes = [vp, P(C.c_double), C.c_double]
+        L.snn_grad_forward.argtypes = [vp, C.c_int64, C.c_int32, P(C.c_double)]
+        L.snn_grad_backward.argtypes = [vp, P(C.c_double), P(C.c_double), P(C.c_double)]
         L.snn_batch_create.argtypes = [P(SnnConfig), P(C.c_uint64), C.c_int32, P(SnnOptions),
                                        vp, P(vp)]
         L.snn_batch_step.argtypes = [vp, C.c_int64]
@@ -296,6 +303,42 @@ class Microcircuit:
         s, a, b = C.c_int64(), C.c_uint64(), C.c_uint64()
         _check(lib().snn_counters(self._h, C.byref(s), C.byref(a), C.byref(b)))
         return {"step": s.value, "spikes": a.value, "events": b.value}
+
+    # -- state, parameters, gradient -------------------------------------------
+    def save_state(self) -> np.ndarray:
+        """The dynamic state as bytes (uint8 array) for :meth:`load_state`."""
+        n = C.c_int64()
+        L = lib()
+        _check(L.snn_save_state(self._h, None, 0, C.byref(n)))
+        buf = np.zeros(n.value, np.uint8)
+        _check(L.snn_save_state(self._h, buf.ctypes.data, buf.size, C.byref(n)))
+        return buf
+
+    def load_state(self, buf: np.ndarray):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        _check(lib().snn_load_state(self._h, buf.ctypes.data, buf.size))
+
+    def set_params(self, scales, nu_bg: float):
+        """Projection weight scales [8][8] (target, source) and background rate."""
+        a = np.ascontiguousarray(np.asarray(scales, np.float64).reshape(MAX_POP * MAX_POP))
+        _check(lib().snn_set_params(self._h, _ptr(a, C.c_double), float(nu_bg)))
+
+    def grad_forward(self, n_steps: int, ckpt_every: int = 100) -> np.ndarray:
+        """Run with checkpoints; population rates (Hz, one per population)."""
+        r = np.zeros(MAX_POP, np.float64)
+        _check(lib().snn_grad_forward(self._h, int(n_steps), int(ckpt_every), _ptr(r, C.c_double)))
+        return r[:len(self.cfg["pop_sizes"])]
+
+    def grad_backward(self, g_rate):
+        """dL/dalpha [8][8] and dL/dnu for g_rate = dL/d(rates)."""
+        g = np.zeros(MAX_POP, np.float64)
+        gr = np.asarray(g_rate, np.float64).reshape(-1)
+        g[:gr.size] = gr
+        ga = np.zeros(MAX_POP * MAX_POP, np.float64)
+        gn = C.c_double()
+        _check(lib().snn_grad_backward(self._h, _ptr(g, C.c_double), _ptr(ga, C.c_double),
+                                       C.byref(gn)))
+        return ga.reshape(MAX_POP, MAX_POP), gn.value
 
     def export_network(self):
         inf = self.info()

@@ -105,32 +105,10 @@ __device__ __forceinline__ int inst_of(const int32_t* s_goff, int n_inst, int32_
     return a;
 }
 
-// full grid barrier on a monotonic counter (reset before every launch);
-// the wait is bounded by time and by the abort flag
-__device__ bool grid_sync(const BatchParams& p, uint32_t& gen, volatile uint32_t* s_abort) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (!(p.inject_fault == 1 && blockIdx.x == 0)) atomicAdd(p.barrier, 1u);
-        const uint32_t target = (gen + 1u) * gridDim.x;
-        const uint64_t t_start = globaltimer_ns();
-        uint32_t iter = 0;
-        while (ld_acquire_gpu(p.barrier) < target) {
-            if ((++iter & 255u) == 0u) {
-                if (ld_relaxed_gpu(p.abort_flag) != 0u) { *s_abort = 1u; break; }
-                if (globaltimer_ns() - t_start > p.timeout_ns) {
-                    atomicOr(p.status, kStatusTimeout);
-                    atomicExch(p.abort_flag, 1u);
-                    *s_abort = 1u;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    ++gen;
-    return *s_abort == 0u;
+__device__ __forceinline__ bool grid_sync(const BatchParams& p, uint32_t& gen,
+                                          volatile uint32_t* s_abort) {
+    return grid_barrier(p.barrier, p.abort_flag, p.status, p.timeout_ns, gen, s_abort,
+                        p.inject_fault == 1 && blockIdx.x == 0);
 }
 
 // Row of global neuron gi, emitted at step t, added into ring slots t + d by

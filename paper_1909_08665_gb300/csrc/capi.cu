@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/snn.h"
+#include "net.h"
 #include "snn_internal.cuh"
 
 namespace snn {
@@ -29,48 +30,6 @@ cudaError_t step_max_blocks(int npt, bool smem_ring, size_t smem, int* blocks_pe
 
 using namespace snn;
 
-struct snn_net {
-    snn_config cfg;
-    uint64_t seed;
-    cudaStream_t stream;
-    int n, n_pop, P, ncmax, npt;
-    bool smem_ring;
-    size_t smem;
-    int32_t pop_start[kMaxPop + 1];
-    std::vector<int32_t> part_lo;
-    uint64_t nnz;
-    int32_t wtab[kMaxPop * kMaxPop * kWCodes];
-    uint8_t dtab[kMaxPop * kDCodes];
-    uint64_t pois[kMaxPop][kPoisTable];
-    uint64_t conn_thr[kMaxPop][kMaxPop];
-    int32_t wext_q, n_ref;
-    float prop[4];
-    float cdc[kMaxPop];
-    int64_t step;
-    uint64_t timeout_ns;
-    uint32_t ras_cap;
-    int32_t inject_fault;
-    // device
-    int32_t* d_part_lo = nullptr;
-    unsigned long long* d_row_start = nullptr;
-    uint32_t* d_seg = nullptr;
-    uint32_t* d_words = nullptr;
-    int32_t* d_wtab = nullptr;
-    uint8_t* d_dtab = nullptr;
-    float* d_u = nullptr;
-    float* d_i = nullptr;
-    int32_t* d_r = nullptr;
-    int32_t* d_ring = nullptr;
-    int2* d_slots = nullptr;               // [P][n][slot_entries] (weight, ring offset)
-    int32_t slot_entries = 0;
-    unsigned long long* d_msg = nullptr;   // [4][P][msg_stride] tagged spike messages
-    int32_t msg_stride = 0;
-    uint32_t* d_ras_step = nullptr;
-    uint32_t* d_ras_id = nullptr;
-    uint32_t* d_ras_n = nullptr;
-    unsigned long long* d_counters = nullptr;
-    uint32_t* d_sync = nullptr;   // [4] status, [5] abort
-};
 
 namespace {
 
@@ -228,9 +187,10 @@ void free_net(snn_net* net) {
     void* ptrs[] = {net->d_part_lo, net->d_row_start, net->d_seg, net->d_words, net->d_wtab,
                     net->d_dtab, net->d_u, net->d_i, net->d_r, net->d_ring, net->d_msg, net->d_slots,
                     net->d_ras_step, net->d_ras_id, net->d_ras_n,
-                    net->d_counters, net->d_sync};
+                    net->d_counters, net->d_sync, net->d_pop_spikes};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    free_grad(net->grad);
     delete net;
 }
 
@@ -310,6 +270,7 @@ int alloc_state(snn_net* net, const float* u0_host) {
     CALL(dalloc(&net->d_ras_n, P, "raster counts"));
     CALL(dalloc(&net->d_counters, 2, "counters"));
     CALL(dalloc(&net->d_sync, 8, "sync words"));
+    CALL(dalloc(&net->d_pop_spikes, kMaxPop, "population spike counters"));
     cudaStream_t s = net->stream;
     CK(cudaMemsetAsync(net->d_i, 0, sizeof(float) * n, s));
     CK(cudaMemsetAsync(net->d_r, 0, sizeof(int32_t) * n, s));
@@ -318,6 +279,7 @@ int alloc_state(snn_net* net, const float* u0_host) {
     CK(cudaMemsetAsync(net->d_ras_n, 0, sizeof(uint32_t) * P, s));
     CK(cudaMemsetAsync(net->d_counters, 0, sizeof(unsigned long long) * 2, s));
     CK(cudaMemsetAsync(net->d_sync, 0, sizeof(uint32_t) * 8, s));
+    CK(cudaMemsetAsync(net->d_pop_spikes, 0, sizeof(unsigned long long) * kMaxPop, s));
     if (u0_host) {
         CK(cudaMemcpyAsync(net->d_u, u0_host, sizeof(float) * n, cudaMemcpyHostToDevice, s));
     } else {
@@ -540,6 +502,95 @@ int build_rows_device(const snn_config* cfg, uint64_t seed, cudaStream_t stream,
     return rc;
 }
 
+void fill_step_params(const snn_net* net, StepParams* out) {
+    StepParams& sp = *out;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.n = net->n;
+    sp.n_pop = net->n_pop;
+    sp.n_part = net->P;
+    sp.ncmax = net->ncmax;
+    for (int p = 0; p <= kMaxPop; ++p) sp.pop_start[p] = net->pop_start[p];
+    sp.P22 = net->prop[0];
+    sp.P21 = net->prop[1];
+    sp.P11 = net->prop[2];
+    sp.theta = (float)net->cfg.theta;
+    for (int p = 0; p < kMaxPop; ++p) sp.cdc[p] = net->cdc[p];
+    sp.n_ref = net->n_ref;
+    sp.wext_q = net->wext_q;
+    sp.mode = net->cfg.input_mode;
+    sp.key0 = (uint32_t)(net->seed & 0xffffffffu);
+    sp.key1 = (uint32_t)(net->seed >> 32);
+    sp.ras_cap = net->ras_cap;
+    sp.timeout_ns = net->timeout_ns;
+    sp.inject_fault = net->inject_fault;
+    for (int p = 0; p < kMaxPop; ++p)
+        for (int m = 0; m < kPoisTable; ++m)   // T >= 1 (validation bounds lambda)
+            sp.pois_m1[p][m] = (uint32_t)(net->pois[p][m] - 1u);
+    sp.slots = net->d_slots;
+    sp.slot_entries = net->slot_entries;
+    sp.part_lo = net->d_part_lo;
+    sp.seg = net->d_seg;
+    sp.words = net->d_words;
+    sp.wtab = net->d_wtab;
+    sp.u = net->d_u;
+    sp.i_syn = net->d_i;
+    sp.refr = net->d_r;
+    sp.ring = net->d_ring;
+    sp.row_start = net->d_row_start;
+    sp.msg = net->d_msg;
+    sp.msg_stride = net->msg_stride;
+    sp.ras_step = net->d_ras_step;
+    sp.ras_id = net->d_ras_id;
+    sp.ras_n = net->d_ras_n;
+    sp.counters = net->d_counters;
+    sp.pop_spikes = net->d_pop_spikes;
+    sp.status = net->d_sync + 4;
+    sp.abort_flag = net->d_sync + 5;
+}
+
+cudaError_t net_launch(snn_net* net, StepParams& sp, int64_t t0, int64_t n) {
+    const int64_t kMaxLaunch = 1ll << 24;
+    int64_t left = n, t = t0;
+    while (left > 0) {
+        const int64_t chunk = std::min(left, kMaxLaunch);
+        sp.t0 = t;
+        sp.n_steps = (int32_t)chunk;
+        cudaError_t e = cudaMemsetAsync(net->d_sync + 5, 0, sizeof(uint32_t), net->stream);
+        if (e == cudaSuccess) e = launch_step(sp, net->npt, net->smem_ring, net->smem, net->stream);
+        if (e != cudaSuccess) return e;
+        t += chunk;
+        left -= chunk;
+    }
+    return cudaSuccess;
+}
+
+int net_make_tables(snn_net* net) { return make_tables(net); }
+
+// unrounded weight of every code at projection scale 1, in pA
+void net_base_weights(const snn_net* net, float* wb) {
+    const snn_config* c = &net->cfg;
+    for (int p = 0; p < kMaxPop; ++p)
+        for (int q = 0; q < kMaxPop; ++q)
+            for (int k = 0; k < kWCodes; ++k) {
+                double w = 0.0;
+                if (p < c->n_pop && q < c->n_pop) {
+                    const double z = norm_quantile(((double)k + 0.5) / (double)kWCodes);
+                    w = (c->w_mean[p][q] + c->w_sd[p][q] * z) * c->w_scale;
+                }
+                wb[(p * kMaxPop + q) * kWCodes + k] = (float)w;
+            }
+}
+
+int net_upload_weights(snn_net* net) {
+    cudaStream_t s = net->stream;
+    CK(cudaMemcpyAsync(net->d_wtab, net->wtab, sizeof(net->wtab), cudaMemcpyHostToDevice, s));
+    CK(launch_build_slots(net->d_words, net->d_seg, net->d_part_lo, net->d_wtab, net->n, net->P,
+                          net->n_pop, net->pop_start, net->ncmax, net->slot_entries, net->d_slots,
+                          s));
+    CK(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
 int set_error(int code, const char* msg) { return fail(code, msg); }
 
 int set_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
@@ -587,59 +638,10 @@ int snn_create_from_rows(const snn_config* cfg, uint64_t seed, const snn_options
 int snn_step(snn_net* net, int64_t n_steps) {
     if (!net) return fail(SNN_ERR_INVALID, "net is NULL");
     if (n_steps < 0) return fail(SNN_ERR_INVALID, "n_steps must be >= 0");
-    const int64_t kMaxLaunch = 1ll << 24;
     StepParams sp;
-    std::memset(&sp, 0, sizeof(sp));
-    sp.n = net->n;
-    sp.n_pop = net->n_pop;
-    sp.n_part = net->P;
-    sp.ncmax = net->ncmax;
-    for (int p = 0; p <= kMaxPop; ++p) sp.pop_start[p] = net->pop_start[p];
-    sp.P22 = net->prop[0];
-    sp.P21 = net->prop[1];
-    sp.P11 = net->prop[2];
-    sp.theta = (float)net->cfg.theta;
-    for (int p = 0; p < kMaxPop; ++p) sp.cdc[p] = net->cdc[p];
-    sp.n_ref = net->n_ref;
-    sp.wext_q = net->wext_q;
-    sp.mode = net->cfg.input_mode;
-    sp.key0 = (uint32_t)(net->seed & 0xffffffffu);
-    sp.key1 = (uint32_t)(net->seed >> 32);
-    sp.ras_cap = net->ras_cap;
-    sp.timeout_ns = net->timeout_ns;
-    sp.inject_fault = net->inject_fault;
-    for (int p = 0; p < kMaxPop; ++p)
-        for (int m = 0; m < kPoisTable; ++m)   // T >= 1 (validation bounds lambda)
-            sp.pois_m1[p][m] = (uint32_t)(net->pois[p][m] - 1u);
-    sp.slots = net->d_slots;
-    sp.slot_entries = net->slot_entries;
-    sp.part_lo = net->d_part_lo;
-    sp.seg = net->d_seg;
-    sp.words = net->d_words;
-    sp.wtab = net->d_wtab;
-    sp.u = net->d_u;
-    sp.i_syn = net->d_i;
-    sp.refr = net->d_r;
-    sp.ring = net->d_ring;
-    sp.row_start = net->d_row_start;
-    sp.msg = net->d_msg;
-    sp.msg_stride = net->msg_stride;
-    sp.ras_step = net->d_ras_step;
-    sp.ras_id = net->d_ras_id;
-    sp.ras_n = net->d_ras_n;
-    sp.counters = net->d_counters;
-    sp.status = net->d_sync + 4;
-    sp.abort_flag = net->d_sync + 5;
-    int64_t left = n_steps;
-    while (left > 0) {
-        const int64_t chunk = std::min(left, kMaxLaunch);
-        sp.t0 = net->step;
-        sp.n_steps = (int32_t)chunk;
-        CK(cudaMemsetAsync(net->d_sync + 5, 0, sizeof(uint32_t), net->stream));
-        CK(launch_step(sp, net->npt, net->smem_ring, net->smem, net->stream));
-        net->step += chunk;
-        left -= chunk;
-    }
+    fill_step_params(net, &sp);
+    CK(net_launch(net, sp, net->step, n_steps));
+    net->step += n_steps;
     return SNN_OK;
 }
 

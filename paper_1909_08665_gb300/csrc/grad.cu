@@ -1,0 +1,587 @@
+// grad.cu -- gradient of a population-rate loss with respect to the 64
+// projection weight scales alpha_pq and the background rate nu, by
+// backpropagation through time over the step recursion of Sec. 2.1 (Eq. 1)
+// with a surrogate spike derivative.  The paper trains nothing; this is the
+// differentiable form of its benchmark network.
+//
+// Model and choices (the same as the CPU reference's hard model):
+//   d s_t / d u_t := 1 / (1 + 10 |u_t - theta|)^2   (fast sigmoid, per mV)
+//   reset and refractory are constants of the backward: the post-spike value
+//   u (1 - s) with s held fixed, and a refractory step passes no gradient;
+//   the fixed-point rounding of alpha w is passed through (d w / d alpha =
+//   w_base, the unrounded weight at alpha = 1) and so is the Poisson count
+//   (d k / d nu = K_ext dt).
+// Adjoint recursion, last step first (lu = dL/du, lI = dL/dI, m_t = 1 when
+// step t took the non-refractory update):
+//   ds_{j,t} = gs[pop j] + sum over row j of (w / 256) lI_{i, t + d}
+//   lu_t = ds_t s'(u_t) + (1 - s_t) m_{t+1} P22 lu_{t+1}
+//   lI_t = P11 lI_{t+1} + m_{t+1} P21 lu_{t+1}
+//   dL/dalpha_pq += s_{j,t} w_base lI_{i,t+d}  (words of j in q into p)
+//   dL/dnu       += lI_{i,t} (w_ext K_ext,p dt)
+//
+// Memory: the forward keeps one checkpoint of the full state (u, I,
+// refractory counters, ring buffers) every `ckpt_every` steps; the backward
+// restores each segment's checkpoint, re-runs the segment with the step
+// kernel recording u (before reset) and the spike / update flags, then runs
+// the adjoint over the segment in one persistent cooperative kernel (one
+// grid barrier per step).  lI of the last 64 steps lives in an adjoint ring
+// [64][n]; per-neuron sums are double and every reduction has a fixed order,
+// so results are deterministic.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/snn.h"
+#include "net.h"
+#include "snn_internal.cuh"
+
+using namespace snn;
+
+struct snn_grad {
+    int64_t t_start = 0;
+    int64_t n_steps = 0;
+    int32_t seg = 0;
+    int32_t n_seg = 0;
+    bool ready = false;
+    size_t ring_words = 0;
+    size_t ckpt_bytes = 0;
+    size_t ckpt_cap = 0;            // checkpoints the buffer holds
+    int32_t tr_cap = 0;             // steps the trace buffers hold
+    uint8_t* ckpt = nullptr;        // [n_seg + 1][u | I | refr | ring]
+    float* tr_u = nullptr;          // [seg][n]
+    uint8_t* tr_f = nullptr;        // [seg][n]
+    float* lu = nullptr;
+    float* lI = nullptr;
+    float* lring = nullptr;         // [64][n]
+    uint8_t* mnext = nullptr;
+    double* gA = nullptr;           // [n][8] by target population
+    double* gN = nullptr;           // [n]
+    float* wbase = nullptr;         // [8][8][128] pA
+    double* out = nullptr;          // [65]
+    uint32_t* sync = nullptr;       // [0] barrier, [1] status, [2] abort
+    unsigned long long* saved = nullptr;   // counters, population counters
+    uint32_t* saved_ras = nullptr;  // raster counts
+    uint32_t* saved_status = nullptr;
+    int32_t* pop_start = nullptr;   // [9]
+};
+
+namespace snn {
+
+void free_grad(snn_grad* g) {
+    if (!g) return;
+    void* ptrs[] = {g->ckpt, g->tr_u, g->tr_f, g->lu, g->lI, g->lring, g->mnext, g->gA, g->gN,
+                    g->wbase, g->out, g->sync, g->saved, g->saved_ras, g->saved_status,
+                    g->pop_start};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete g;
+}
+
+void net_base_weights(const snn_net* net, float* wb);
+
+}  // namespace snn
+
+namespace {
+
+constexpr int kAdjThreads = 512;
+constexpr int kAdjWarps = kAdjThreads / 32;
+
+struct AdjParams {
+    int32_t n, n_pop, len, chunk;
+    int32_t pop_start[kMaxPop + 1];
+    int64_t t_first;                 // global step of trace row 0
+    float P22, P21, P11, theta;
+    float gs[kMaxPop];               // dL/ds per spike of each population
+    uint64_t timeout_ns;
+    const unsigned long long* row_start;
+    const uint32_t* words;
+    const int32_t* wtab;             // rounded weights of the forward, 1/256 pA
+    const float* wbase;
+    const float* tr_u;
+    const uint8_t* tr_f;
+    float* lu;
+    float* lI;
+    float* lring;
+    uint8_t* mnext;
+    double* gA;
+    double* gN;
+    uint32_t* barrier;
+    uint32_t* status;
+    uint32_t* abort_flag;
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// fast-sigmoid derivative 1 / (1 + 10 |x|)^2
+__device__ __forceinline__ float surrogate_slope(float x) {
+    const float a = __fadd_rn(1.0f, __fmul_rn(10.0f, fabsf(x)));
+    return __fdiv_rn(1.0f, __fmul_rn(a, a));
+}
+
+// The adjoint of trace rows len-1 .. 0.  CTA b owns neurons
+// [b chunk, (b + 1) chunk): their rows in the spike phase and their state in
+// the membrane phase; one grid barrier per step separates the lI writes of
+// step t from the row gathers of step t - 1.
+__global__ void __launch_bounds__(kAdjThreads, 1) k_adjoint(const __grid_constant__ AdjParams p) {
+    extern __shared__ float s_ds[];                   // [chunk]
+    __shared__ volatile uint32_t s_abort;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t lo = min(p.n, (int32_t)blockIdx.x * p.chunk);
+    const int32_t hi = min(p.n, lo + p.chunk);
+    if (tid == 0) s_abort = 0u;
+    __syncthreads();
+    const size_t n = (size_t)p.n;
+    uint32_t gen = 0;
+    for (int s = p.len - 1; s >= 0; --s) {
+        const int64_t t = p.t_first + s;
+        const uint8_t* fl = p.tr_f + (size_t)s * n;
+        // ---- spike adjoints: loss term plus the rows' pull from lI(t + d) ----
+        for (int32_t j = lo + warp; j < hi; j += kAdjWarps) {
+            const int q = pop_index(p.pop_start, p.n_pop, j);
+            const bool spk = (fl[j] & 1u) != 0u;
+            int32_t ps[kMaxPop];
+#pragma unroll
+            for (int k = 1; k < kMaxPop; ++k) ps[k] = k < p.n_pop ? p.pop_start[k] : 0x7fffffff;
+            const int32_t* wq = p.wtab + q * kWCodes;
+            const float* bq = p.wbase + q * kWCodes;
+            float acc = 0.f;
+            float pa[kMaxPop];
+#pragma unroll
+            for (int k = 0; k < kMaxPop; ++k) pa[k] = 0.f;
+            const unsigned long long b = p.row_start[j], e = p.row_start[j + 1];
+            for (unsigned long long w = b + lane; w < e; w += 32) {
+                const uint32_t word = __ldg(&p.words[w]);
+                const int32_t tgt = (int32_t)(word & kTgtMask);
+                int pp = 0;
+#pragma unroll
+                for (int k = 1; k < kMaxPop; ++k) pp += tgt >= ps[k] ? 1 : 0;
+                const int code = (int)(word >> 25);
+                const uint32_t slot = (uint32_t)(t + ((word >> kTgtBits) & 63u)) & (kRing - 1);
+                const float l = __ldcg(&p.lring[(size_t)slot * n + tgt]);
+                const float wt = __fmul_rn(__int2float_rn(__ldg(&wq[pp * (kMaxPop * kWCodes) + code])),
+                                           0.00390625f);
+                acc = __fadd_rn(acc, __fmul_rn(wt, l));
+                if (spk) {
+                    const float v = __fmul_rn(__ldg(&bq[pp * (kMaxPop * kWCodes) + code]), l);
+#pragma unroll
+                    for (int k = 0; k < kMaxPop; ++k) pa[k] = __fadd_rn(pa[k], k == pp ? v : 0.f);
+                }
+            }
+            acc = warp_sum(acc);
+            if (spk) {
+#pragma unroll
+                for (int k = 0; k < kMaxPop; ++k) pa[k] = warp_sum(pa[k]);
+            }
+            if (lane == 0) {
+                s_ds[j - lo] = __fadd_rn(p.gs[q], acc);
+                if (spk) {
+#pragma unroll
+                    for (int k = 0; k < kMaxPop; ++k)
+                        if (k < p.n_pop) p.gA[(size_t)j * kMaxPop + k] += (double)pa[k];
+                }
+            }
+        }
+        __syncthreads();
+        // ---- membrane and current adjoints of step t ----
+        const float* ut = p.tr_u + (size_t)s * n;
+        for (int32_t i = lo + tid; i < hi; i += kAdjThreads) {
+            const uint8_t f = fl[i];
+            const bool mn = p.mnext[i] != 0u;
+            const float lu1 = p.lu[i];
+            const float lub = mn ? __fmul_rn(p.P22, lu1) : 0.f;
+            const float lIt = __fadd_rn(__fmul_rn(p.P11, p.lI[i]), mn ? __fmul_rn(p.P21, lu1) : 0.f);
+            const float sv = (f & 1u) ? 1.f : 0.f;
+            const float lut = __fadd_rn(__fmul_rn(s_ds[i - lo], surrogate_slope(__fsub_rn(ut[i], p.theta))),
+                                        __fmul_rn(__fsub_rn(1.f, sv), lub));
+            p.lu[i] = lut;
+            p.lI[i] = lIt;
+            p.mnext[i] = (uint8_t)((f >> 1) & 1u);
+            __stcg(&p.lring[(size_t)((uint32_t)t & (kRing - 1)) * n + i], lIt);
+            p.gN[i] += (double)lIt;
+        }
+        if (!grid_barrier(p.barrier, p.abort_flag, p.status, p.timeout_ns, gen, &s_abort, false))
+            break;
+    }
+}
+
+// dL/dalpha_pq = sum over j in q of gA[j][p]; dL/dnu = sum_j gN[j] dnu[pop j].
+// One CTA, every output reduced in the same fixed order.
+__global__ void __launch_bounds__(512) k_grad_reduce(int32_t n, int32_t n_pop,
+                                                     const int32_t* __restrict__ pop_start_dev,
+                                                     const double* __restrict__ gA,
+                                                     const double* __restrict__ gN,
+                                                     const double* __restrict__ dnu, double* out) {
+    __shared__ double red[512];
+    __shared__ int32_t ps[kMaxPop + 1];
+    const int tid = threadIdx.x;
+    if (tid <= kMaxPop) ps[tid] = pop_start_dev[tid];
+    __syncthreads();
+    for (int o = 0; o <= kMaxPop * kMaxPop; ++o) {
+        double v = 0.0;
+        if (o < kMaxPop * kMaxPop) {
+            const int p = o / kMaxPop, q = o % kMaxPop;
+            if (p < n_pop && q < n_pop)
+                for (int32_t j = ps[q] + tid; j < ps[q + 1]; j += 512) v += gA[(size_t)j * kMaxPop + p];
+        } else {
+            for (int32_t j = tid; j < n; j += 512) v += gN[j] * dnu[pop_index(ps, n_pop, j)];
+        }
+        red[tid] = v;
+        __syncthreads();
+        for (int w = 256; w > 0; w >>= 1) {
+            if (tid < w) red[tid] += red[tid + w];
+            __syncthreads();
+        }
+        if (tid == 0) out[o] = red[0];
+        __syncthreads();
+    }
+}
+
+#define GCK(call)                                                     \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return set_cuda_error(e_, #call);      \
+    } while (0)
+
+template <typename T>
+int galloc(T** p, size_t count, const char* what) {
+    if (*p) return SNN_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_error(SNN_ERR_OOM, what);
+    }
+    return SNN_OK;
+}
+
+#define GCALL(x)                        \
+    do {                                \
+        int rc_ = (x);                  \
+        if (rc_ != SNN_OK) return rc_;  \
+    } while (0)
+
+size_t ring_words(const snn_net* net) { return (size_t)net->P * kRing * net->ncmax; }
+
+size_t state_bytes(const snn_net* net) {
+    return (size_t)net->n * 12 + ring_words(net) * sizeof(int32_t);
+}
+
+// copy the full device state to / from one checkpoint slot
+cudaError_t save_ckpt(snn_net* net, uint8_t* dst) {
+    const size_t n = (size_t)net->n;
+    cudaStream_t s = net->stream;
+    cudaError_t e = cudaMemcpyAsync(dst, net->d_u, n * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst + n * 4, net->d_i, n * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst + n * 8, net->d_r, n * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dst + n * 12, net->d_ring, ring_words(net) * 4, cudaMemcpyDeviceToDevice, s);
+    return e;
+}
+
+// the spike messages carry step tags: clear them whenever the state is
+// rewound, so that no message of an abandoned future can match a tag again
+cudaError_t clear_messages(snn_net* net) {
+    return cudaMemsetAsync(net->d_msg, 0, sizeof(unsigned long long) * 4 * net->P * net->msg_stride,
+                           net->stream);
+}
+
+cudaError_t load_ckpt(snn_net* net, const uint8_t* src) {
+    const size_t n = (size_t)net->n;
+    cudaStream_t s = net->stream;
+    cudaError_t e = cudaMemcpyAsync(net->d_u, src, n * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(net->d_i, src + n * 4, n * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(net->d_r, src + n * 8, n * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(net->d_ring, src + n * 12, ring_words(net) * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = clear_messages(net);
+    return e;
+}
+
+constexpr uint64_t kStateMagic = 0x3145544154534e53ull;   // "SNSTATE1"
+
+}  // namespace
+
+extern "C" {
+
+int snn_set_params(snn_net* net, const double* scales, double nu_bg) {
+    if (!net || !scales) return set_error(SNN_ERR_INVALID, "bad arguments");
+    snn_config c = net->cfg;
+    for (int p = 0; p < kMaxPop; ++p)
+        for (int q = 0; q < kMaxPop; ++q) {
+            const double a = scales[p * kMaxPop + q];
+            if (!std::isfinite(a)) return set_error(SNN_ERR_INVALID, "scales must be finite");
+            c.proj_scale[p][q] = a;
+        }
+    if (!(nu_bg >= 0) || !std::isfinite(nu_bg)) return set_error(SNN_ERR_INVALID, "nu_bg must be >= 0");
+    c.nu_bg = nu_bg;
+    for (int p = 0; p < c.n_pop; ++p)
+        if (nu_bg * c.k_ext[p] * (c.dt / 1000.0) > 20.0)
+            return set_error(SNN_ERR_INVALID, "background mean per step above 20 spikes");
+    GCK(cudaStreamSynchronize(net->stream));
+    const snn_config old = net->cfg;
+    net->cfg = c;
+    int rc = net_make_tables(net);
+    if (rc != SNN_OK) {
+        net->cfg = old;
+        net_make_tables(net);
+        return rc;
+    }
+    if (net->grad) net->grad->ready = false;
+    return net_upload_weights(net);
+}
+
+int snn_grad_forward(snn_net* net, int64_t n_steps, int32_t ckpt_every, double* rates_host) {
+    if (!net || n_steps < 1 || ckpt_every < 1 || !rates_host)
+        return set_error(SNN_ERR_INVALID, "bad arguments");
+    if (n_steps > (1ll << 31)) return set_error(SNN_ERR_INVALID, "n_steps too large");
+    if (!net->grad) net->grad = new snn_grad();
+    snn_grad* g = net->grad;
+    const int n = net->n;
+    const int32_t seg = (int32_t)std::min<int64_t>(ckpt_every, n_steps);
+    const int32_t n_seg = (int32_t)((n_steps + seg - 1) / seg);
+    g->ready = false;
+    g->ring_words = ring_words(net);
+    g->ckpt_bytes = (state_bytes(net) + 255) / 256 * 256;
+    if (g->ckpt && g->ckpt_cap < (size_t)n_seg + 1) {
+        cudaFree(g->ckpt);
+        g->ckpt = nullptr;
+    }
+    if (!g->ckpt) {
+        GCALL(galloc(&g->ckpt, g->ckpt_bytes * ((size_t)n_seg + 1), "gradient checkpoints"));
+        g->ckpt_cap = (size_t)n_seg + 1;
+    }
+    if (g->tr_u && g->tr_cap < seg) {
+        cudaFree(g->tr_u);
+        cudaFree(g->tr_f);
+        g->tr_u = nullptr;
+        g->tr_f = nullptr;
+    }
+    GCALL(galloc(&g->tr_u, (size_t)seg * n, "gradient trace"));
+    GCALL(galloc(&g->tr_f, (size_t)seg * n, "gradient trace"));
+    g->tr_cap = std::max(g->tr_cap, seg);
+    cudaStream_t s = net->stream;
+    GCK(cudaMemsetAsync(net->d_pop_spikes, 0, sizeof(unsigned long long) * kMaxPop, s));
+    StepParams sp;
+    fill_step_params(net, &sp);
+    const int64_t t0 = net->step;
+    for (int32_t c = 0; c < n_seg; ++c) {
+        GCK(save_ckpt(net, g->ckpt + (size_t)c * g->ckpt_bytes));
+        const int64_t len = std::min<int64_t>(seg, n_steps - (int64_t)c * seg);
+        GCK(net_launch(net, sp, t0 + (int64_t)c * seg, len));
+    }
+    GCK(save_ckpt(net, g->ckpt + (size_t)n_seg * g->ckpt_bytes));
+    unsigned long long cnt[kMaxPop];
+    GCK(cudaMemcpyAsync(cnt, net->d_pop_spikes, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    GCK(cudaStreamSynchronize(s));
+    net->step = t0 + n_steps;
+    uint32_t st = 0;
+    GCK(cudaMemcpy(&st, net->d_sync + 4, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st & kStatusTimeout) return set_error(SNN_ERR_TIMEOUT, "a grid-barrier wait timed out");
+    const double T = (double)n_steps * net->cfg.dt / 1000.0;
+    for (int p = 0; p < kMaxPop; ++p)
+        rates_host[p] = (p < net->n_pop && net->cfg.pop_size[p] > 0)
+                            ? (double)cnt[p] / ((double)net->cfg.pop_size[p] * T)
+                            : 0.0;
+    g->t_start = t0;
+    g->n_steps = n_steps;
+    g->seg = seg;
+    g->n_seg = n_seg;
+    g->ready = true;
+    return SNN_OK;
+}
+
+int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, double* g_nu) {
+    if (!net || !g_rate || !g_alpha || !g_nu) return set_error(SNN_ERR_INVALID, "bad arguments");
+    snn_grad* g = net->grad;
+    if (!g || !g->ready) return set_error(SNN_ERR_INVALID, "no gradient forward to differentiate");
+    if (net->step != g->t_start + g->n_steps)
+        return set_error(SNN_ERR_INVALID, "the network was stepped after the gradient forward");
+    const int n = net->n, P = net->P;
+    cudaStream_t s = net->stream;
+    GCALL(galloc(&g->lu, n, "adjoint"));
+    GCALL(galloc(&g->lI, n, "adjoint"));
+    GCALL(galloc(&g->lring, (size_t)kRing * n, "adjoint ring"));
+    GCALL(galloc(&g->mnext, n, "adjoint"));
+    GCALL(galloc(&g->gA, (size_t)n * kMaxPop, "gradient sums"));
+    GCALL(galloc(&g->gN, n, "gradient sums"));
+    GCALL(galloc(&g->wbase, kMaxPop * kMaxPop * kWCodes, "base weights"));
+    GCALL(galloc(&g->out, kMaxPop * kMaxPop + 1 + kMaxPop, "gradient output"));
+    GCALL(galloc(&g->sync, 4, "adjoint barrier"));
+    GCALL(galloc(&g->saved, 2 + kMaxPop, "saved counters"));
+    GCALL(galloc(&g->saved_ras, P, "saved raster counts"));
+    GCALL(galloc(&g->saved_status, 1, "saved status"));
+    GCALL(galloc(&g->pop_start, kMaxPop + 1, "population starts"));
+    // keep the caller-visible counters, raster counts and status: the
+    // recomputation re-runs steps that were already counted and recorded
+    GCK(cudaMemcpyAsync(g->saved, net->d_counters, 16, cudaMemcpyDeviceToDevice, s));
+    GCK(cudaMemcpyAsync(g->saved + 2, net->d_pop_spikes, 8 * kMaxPop, cudaMemcpyDeviceToDevice, s));
+    GCK(cudaMemcpyAsync(g->saved_ras, net->d_ras_n, 4 * P, cudaMemcpyDeviceToDevice, s));
+    GCK(cudaMemcpyAsync(g->saved_status, net->d_sync + 4, 4, cudaMemcpyDeviceToDevice, s));
+    GCK(cudaMemsetAsync(g->lu, 0, sizeof(float) * n, s));
+    GCK(cudaMemsetAsync(g->lI, 0, sizeof(float) * n, s));
+    GCK(cudaMemsetAsync(g->lring, 0, sizeof(float) * (size_t)kRing * n, s));
+    GCK(cudaMemsetAsync(g->mnext, 0, n, s));
+    GCK(cudaMemsetAsync(g->gA, 0, sizeof(double) * (size_t)n * kMaxPop, s));
+    GCK(cudaMemsetAsync(g->gN, 0, sizeof(double) * n, s));
+    GCK(cudaMemsetAsync(g->sync, 0, sizeof(uint32_t) * 4, s));
+    std::vector<float> wb(kMaxPop * kMaxPop * kWCodes);
+    net_base_weights(net, wb.data());
+    GCK(cudaMemcpyAsync(g->wbase, wb.data(), sizeof(float) * wb.size(), cudaMemcpyHostToDevice, s));
+    // dnu per population and the population starts for the reduction
+    const double dts = net->cfg.dt / 1000.0;
+    double dnu[kMaxPop];
+    for (int p = 0; p < kMaxPop; ++p)
+        dnu[p] = (p < net->n_pop && net->cfg.input_mode == 0)
+                     ? (double)net->wext_q / 256.0 * net->cfg.k_ext[p] * dts
+                     : 0.0;
+    GCK(cudaMemcpyAsync(g->out + kMaxPop * kMaxPop + 1, dnu, sizeof(dnu), cudaMemcpyHostToDevice, s));
+    GCK(cudaMemcpyAsync(g->pop_start, net->pop_start, sizeof(int32_t) * (kMaxPop + 1), cudaMemcpyHostToDevice, s));
+
+    int dev = 0, sms = 0;
+    GCK(cudaGetDevice(&dev));
+    GCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = std::max(1, std::min(sms, (n + 31) / 32));
+    AdjParams ap;
+    std::memset(&ap, 0, sizeof(ap));
+    ap.n = n;
+    ap.n_pop = net->n_pop;
+    ap.chunk = (n + grid - 1) / grid;
+    for (int p = 0; p <= kMaxPop; ++p) ap.pop_start[p] = net->pop_start[p];
+    ap.P22 = net->prop[0];
+    ap.P21 = net->prop[1];
+    ap.P11 = net->prop[2];
+    ap.theta = (float)net->cfg.theta;
+    const double T = (double)g->n_steps * net->cfg.dt / 1000.0;
+    for (int p = 0; p < kMaxPop; ++p)
+        ap.gs[p] = (p < net->n_pop && net->cfg.pop_size[p] > 0)
+                       ? (float)(g_rate[p] / ((double)net->cfg.pop_size[p] * T))
+                       : 0.f;
+    ap.timeout_ns = net->timeout_ns;
+    ap.row_start = net->d_row_start;
+    ap.words = net->d_words;
+    ap.wtab = net->d_wtab;
+    ap.wbase = g->wbase;
+    ap.tr_u = g->tr_u;
+    ap.tr_f = g->tr_f;
+    ap.lu = g->lu;
+    ap.lI = g->lI;
+    ap.lring = g->lring;
+    ap.mnext = g->mnext;
+    ap.gA = g->gA;
+    ap.gN = g->gN;
+    ap.barrier = g->sync;
+    ap.status = g->sync + 1;
+    ap.abort_flag = g->sync + 2;
+    const size_t smem = sizeof(float) * (size_t)ap.chunk;
+    GCK(cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+
+    StepParams sp;
+    fill_step_params(net, &sp);
+    sp.pop_spikes = nullptr;
+    sp.tr_u = g->tr_u;
+    sp.tr_f = g->tr_f;
+    for (int32_t c = g->n_seg - 1; c >= 0; --c) {
+        const int64_t t0 = g->t_start + (int64_t)c * g->seg;
+        const int32_t len = (int32_t)std::min<int64_t>(g->seg, g->n_steps - (int64_t)c * g->seg);
+        GCK(load_ckpt(net, g->ckpt + (size_t)c * g->ckpt_bytes));
+        sp.tr_t0 = t0;
+        sp.tr_len = len;
+        GCK(net_launch(net, sp, t0, len));
+        ap.t_first = t0;
+        ap.len = len;
+        GCK(cudaMemsetAsync(g->sync, 0, sizeof(uint32_t), s));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kAdjThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        void* args[] = {&ap};
+        GCK(cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(&k_adjoint), args));
+    }
+    k_grad_reduce<<<1, 512, 0, s>>>(n, net->n_pop, g->pop_start, g->gA, g->gN, g->out + kMaxPop * kMaxPop + 1,
+                                     g->out);
+    GCK(cudaGetLastError());
+    // back to the state after the forward, with the caller's counters
+    GCK(load_ckpt(net, g->ckpt + (size_t)g->n_seg * g->ckpt_bytes));
+    GCK(cudaMemcpyAsync(net->d_counters, g->saved, 16, cudaMemcpyDeviceToDevice, s));
+    GCK(cudaMemcpyAsync(net->d_pop_spikes, g->saved + 2, 8 * kMaxPop, cudaMemcpyDeviceToDevice, s));
+    GCK(cudaMemcpyAsync(net->d_ras_n, g->saved_ras, 4 * P, cudaMemcpyDeviceToDevice, s));
+    GCK(cudaMemcpyAsync(net->d_sync + 4, g->saved_status, 4, cudaMemcpyDeviceToDevice, s));
+    double out[kMaxPop * kMaxPop + 1];
+    GCK(cudaMemcpyAsync(out, g->out, sizeof(out), cudaMemcpyDeviceToHost, s));
+    uint32_t adj_status = 0;
+    GCK(cudaMemcpyAsync(&adj_status, g->sync + 1, sizeof(adj_status), cudaMemcpyDeviceToHost, s));
+    GCK(cudaStreamSynchronize(s));
+    if (adj_status & kStatusTimeout) return set_error(SNN_ERR_TIMEOUT, "an adjoint barrier wait timed out");
+    for (int k = 0; k < kMaxPop * kMaxPop; ++k) g_alpha[k] = out[k];
+    *g_nu = out[kMaxPop * kMaxPop];
+    return SNN_OK;
+}
+
+int snn_save_state(snn_net* net, void* buf_host, int64_t cap, int64_t* n_bytes) {
+    if (!net || !n_bytes) return set_error(SNN_ERR_INVALID, "bad arguments");
+    const size_t n = (size_t)net->n;
+    const size_t need = 32 + n * 12 + (size_t)kRing * n * 4;
+    *n_bytes = (int64_t)need;
+    if (!buf_host) return SNN_OK;
+    if (cap < (int64_t)need) return set_error(SNN_ERR_INVALID, "buffer smaller than the state");
+    GCK(cudaStreamSynchronize(net->stream));
+    uint8_t* b = static_cast<uint8_t*>(buf_host);
+    const uint64_t hdr[4] = {kStateMagic, (uint64_t)n, (uint64_t)net->step, (uint64_t)kRing};
+    std::memcpy(b, hdr, 32);
+    GCK(cudaMemcpy(b + 32, net->d_u, n * 4, cudaMemcpyDeviceToHost));
+    GCK(cudaMemcpy(b + 32 + n * 4, net->d_i, n * 4, cudaMemcpyDeviceToHost));
+    GCK(cudaMemcpy(b + 32 + n * 8, net->d_r, n * 4, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> tmp(ring_words(net));
+    GCK(cudaMemcpy(tmp.data(), net->d_ring, tmp.size() * 4, cudaMemcpyDeviceToHost));
+    int32_t* ring = reinterpret_cast<int32_t*>(b + 32 + n * 12);
+    for (int c = 0; c < net->P; ++c) {
+        const int lo = net->part_lo[c], nc = net->part_lo[c + 1] - lo;
+        for (int slot = 0; slot < kRing; ++slot)
+            std::memcpy(ring + (size_t)slot * n + lo, tmp.data() + ((size_t)c * kRing + slot) * net->ncmax,
+                        sizeof(int32_t) * nc);
+    }
+    return SNN_OK;
+}
+
+int snn_load_state(snn_net* net, const void* buf_host, int64_t n_bytes) {
+    if (!net || !buf_host) return set_error(SNN_ERR_INVALID, "bad arguments");
+    const size_t n = (size_t)net->n;
+    const size_t need = 32 + n * 12 + (size_t)kRing * n * 4;
+    if (n_bytes != (int64_t)need) return set_error(SNN_ERR_INVALID, "state size does not match the network");
+    const uint8_t* b = static_cast<const uint8_t*>(buf_host);
+    uint64_t hdr[4];
+    std::memcpy(hdr, b, 32);
+    if (hdr[0] != kStateMagic || hdr[1] != (uint64_t)n || hdr[3] != (uint64_t)kRing)
+        return set_error(SNN_ERR_INVALID, "not a state of this network");
+    std::vector<int32_t> tmp(ring_words(net), 0);
+    const int32_t* ring = reinterpret_cast<const int32_t*>(b + 32 + n * 12);
+    for (int c = 0; c < net->P; ++c) {
+        const int lo = net->part_lo[c], nc = net->part_lo[c + 1] - lo;
+        for (int slot = 0; slot < kRing; ++slot)
+            std::memcpy(tmp.data() + ((size_t)c * kRing + slot) * net->ncmax, ring + (size_t)slot * n + lo,
+                        sizeof(int32_t) * nc);
+    }
+    GCK(cudaStreamSynchronize(net->stream));
+    GCK(cudaMemcpy(net->d_u, b + 32, n * 4, cudaMemcpyHostToDevice));
+    GCK(cudaMemcpy(net->d_i, b + 32 + n * 4, n * 4, cudaMemcpyHostToDevice));
+    GCK(cudaMemcpy(net->d_r, b + 32 + n * 8, n * 4, cudaMemcpyHostToDevice));
+    GCK(cudaMemcpy(net->d_ring, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice));
+    GCK(clear_messages(net));
+    GCK(cudaStreamSynchronize(net->stream));
+    net->step = (int64_t)hdr[2];
+    if (net->grad) net->grad->ready = false;
+    return SNN_OK;
+}
+
+}  // extern "C"

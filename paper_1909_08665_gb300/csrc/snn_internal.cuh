@@ -72,6 +72,41 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
+// Full grid barrier of a cooperative launch on a monotonic arrival counter
+// (zeroed before the launch): barrier number `gen` completes when the counter
+// reaches (gen + 1) * gridDim.x.  The wait is bounded: it gives up when
+// another CTA raised the abort flag, or after timeout_ns, when it sets the
+// timeout status bit and the abort flag itself.  skip_arrive withholds this
+// CTA's arrival (tests of the bounded wait).  Returns false once aborted.
+__device__ __forceinline__ bool grid_barrier(uint32_t* counter, uint32_t* abort_flag,
+                                             uint32_t* status, uint64_t timeout_ns,
+                                             uint32_t& gen, volatile uint32_t* s_abort,
+                                             bool skip_arrive) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (!skip_arrive) atomicAdd(counter, 1u);
+        const uint32_t target = (gen + 1u) * gridDim.x;
+        const uint64_t t_start = globaltimer_ns();
+        uint32_t iter = 0;
+        while (ld_acquire_gpu(counter) < target) {
+            if ((++iter & 255u) == 0u) {
+                if (ld_relaxed_gpu(abort_flag) != 0u) { *s_abort = 1u; break; }
+                if (globaltimer_ns() - t_start > timeout_ns) {
+                    atomicOr(status, kStatusTimeout);
+                    atomicExch(abort_flag, 1u);
+                    *s_abort = 1u;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    ++gen;
+    return *s_abort == 0u;
+}
+
 // ---------------------------------------------------------------------------
 // parameters
 // ---------------------------------------------------------------------------
@@ -134,8 +169,16 @@ struct StepParams {
     uint32_t* ras_id;
     uint32_t* ras_n;                    // [n_part] spikes recorded (may exceed cap)
     unsigned long long* counters;       // [0] spikes, [1] synaptic events
+    unsigned long long* pop_spikes;     // [8] spikes per population
     uint32_t* status;
     uint32_t* abort_flag;
+    // optional per-step record for the gradient: for steps t in
+    // [tr_t0, tr_t0 + tr_len), tr_u[(t - tr_t0) n + i] = u after the
+    // membrane update (before reset), tr_f = spike | non-refractory << 1
+    float* tr_u;
+    uint8_t* tr_f;
+    int64_t tr_t0;
+    int32_t tr_len;
 };
 
 struct DeliverParams {

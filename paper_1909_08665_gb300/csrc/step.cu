@@ -374,6 +374,7 @@ k_step(const __grid_constant__ StepParams sp) {
             const int li = tid + k * kStepThreads;
             bool spk = false;
             if (li < nc) {
+                uint8_t upd = 0;
                 if (refr[k] > 0) {
                     refr[k] -= 1;
                     u[k] = 0.f;
@@ -381,11 +382,19 @@ k_step(const __grid_constant__ StepParams sp) {
                     float v = __fadd_rn(__fmul_rn(sp.P22, u[k]), __fmul_rn(sp.P21, isyn[k]));
                     if (sp.mode == 1) v = __fadd_rn(v, sp.cdc[pop[k]]);
                     u[k] = v;
+                    upd = 2;
                 }
+                const float upre = u[k];
                 if (u[k] > sp.theta) {
                     spk = true;
                     u[k] = 0.f;
                     refr[k] = sp.n_ref;
+                    if (sp.pop_spikes) atomicAdd(&sp.pop_spikes[pop[k]], 1ull);
+                }
+                if (sp.tr_u != nullptr && t >= sp.tr_t0 && t < sp.tr_t0 + sp.tr_len) {
+                    const size_t o = (size_t)(t - sp.tr_t0) * (size_t)sp.n + (size_t)(lo + li);
+                    sp.tr_u[o] = upre;
+                    sp.tr_f[o] = (uint8_t)(upd | (spk ? 1 : 0));
                 }
             }
             const unsigned mask = __ballot_sync(0xffffffffu, spk);
