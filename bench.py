@@ -19,6 +19,14 @@ Printed JSON line (rank 0):
 
 --impl reference times the CPU oracle itself (the reference arm).
 Multi-GPU (torchrun, --gpus N): N independent replicas, one per GPU.
+
+Other workloads (--workload; the default line is the full microcircuit):
+  scale4  the 4x microcircuit (308,676 neurons, ~1.2e9 synapses), same metric
+  batch   64 independent microcircuits at scales U(0.05, 0.25) in one
+          persistent kernel replayed from a CUDA graph; 1 step = 1 s
+          biological of every instance; synaptic events/s over all instances
+  grad    one surrogate-gradient evaluation (forward with checkpoints every
+          100 steps + backward) of the 10 % microcircuit over 200 ms
 """
 import argparse
 import json
@@ -266,9 +274,11 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/i32", "data": "synthetic",
         "real_time_factor": rtf,
-        "config": {"workload": "full microcircuit, 77,169 LIF neurons, %d synapses, Poisson "
-                               "background, dt 0.1 ms; 1 step = 10,000 time steps (1 s biological)"
-                               % info["n_synapses"],
+        "config": {"workload": "%s, %d LIF neurons, %d synapses, Poisson background, dt 0.1 "
+                               "ms; 1 step = %d time steps (%g s biological)"
+                               % ("full microcircuit" if args.scale == 1.0
+                                  else "%gx microcircuit (same in-degrees)" % args.scale,
+                                  info["n_neurons"], info["n_synapses"], chunk, chunk * 1e-4),
                    "scale": args.scale, "seed": cfg["seed"], "time_steps_per_step": chunk,
                    "l2": "no flush: synapse rows (%.2f GB) exceed the 129 MB L2"
                          % (info["n_synapses"] * 4 / 1e9),
@@ -287,7 +297,7 @@ def run_ours(args):
                      "frac": achieved / hbm_peak, "traffic": None,
                      "peak_kind": peak_kind, "kernel": "k_step (persistent step kernel)"},
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.scale <= 1.0:
         line["cpu_baseline"] = cpu_baseline(cfg, os.cpu_count() or 1, args.cpu_skip,
                                             args.cpu_steps)
     if rank == 0:
@@ -296,6 +306,151 @@ def run_ours(args):
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_batch(args):
+    import torch
+
+    import paper_1909_08665_gb300 as pkg
+    import workload
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    cfgs = workload.batched_instances(64, seed=7 + rank)
+    t_build = time.time()
+    b = pkg.MicrocircuitBatch(cfgs, stream=stream)
+    build_s = time.time() - t_build
+    info = b.info(0)
+    chunk = args.chunk
+    for _ in range(args.warmup):
+        b.step(chunk)
+    b.sync()
+    for k in range(len(b)):
+        b.read_spikes(k)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize(dev)
+
+    ev0 = sum(b.counters(k)["events"] for k in range(len(b)))
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            starts[k].record(stream)
+            b.step(chunk)
+            ends[k].record(stream)
+        barrier()
+    b.sync()
+    ev1 = sum(b.counters(k)["events"] for k in range(len(b)))
+    total_ms = starts[0].elapsed_time(ends[-1])
+    events = ev1 - ev0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        e = torch.tensor([float(events)], device=dev, dtype=torch.float64)
+        dist.all_reduce(e)
+        events_all = float(e.item())
+    else:
+        events_all = float(events)
+    bio_s = args.steps * chunk * 1e-4
+    launches_per_step = chunk // info["graph_steps"] + (1 if chunk % info["graph_steps"] else 0)
+    avg_launch_s = total_ms * 1e-3 / (args.steps * launches_per_step)
+    hbm_peak, peak_kind = load_peaks()
+    achieved = BYTES_PER_EVENT * (events / (args.steps * launches_per_step)) / avg_launch_s / 1e9
+    tilings = [b.info(k)["tiling"] for k in range(len(b))]
+    line = {
+        "metric": METRIC, "value": events_all / (total_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/i32",
+        "data": "synthetic", "real_time_factor": total_ms * 1e-3 / bio_s,
+        "config": {"workload": "64 independent microcircuits, scales U(0.05, 0.25) (seed 7), "
+                               "%d neurons in total, one persistent kernel per graph replay of "
+                               "%d time steps; 1 step = %d time steps of every instance"
+                               % (info["n_neurons_total"], info["graph_steps"], chunk),
+                   "time_steps_per_step": chunk, "instances": len(b),
+                   "tilings": {"warp_per_spike": tilings.count(0),
+                               "block_per_row": tilings.count(1)},
+                   "l2": "no flush: the 64 instances' synapse rows and ring buffers exceed L2",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "us_per_time_step": total_ms * 1e3 / (args.steps * chunk),
+        "events_per_time_step": events / (args.steps * chunk),
+        "build_s": build_s, "clocks": clk.summary(),
+        "gpu_launches": args.steps * launches_per_step,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_batch (persistent batched step kernel)"},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_grad(args):
+    import torch
+
+    import paper_1909_08665_gb300 as pkg
+    from paper_1909_08665_gb300.autograd import microcircuit_rates
+    import workload
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    cfg = workload.microcircuit(0.1, seed=12345 + rank)
+    targets = torch.as_tensor(workload.target_rates())
+    net = pkg.Microcircuit(cfg, stream=stream)
+    start = net.save_state()
+    n_steps, every = 2000, 100
+
+    def one():
+        scales = torch.ones(8, 8, dtype=torch.float64, requires_grad=True)
+        nu = torch.tensor(float(cfg["nu_bg"]), dtype=torch.float64, requires_grad=True)
+        rates = microcircuit_rates(scales, nu, net, n_steps, every, start)
+        loss = ((rates - targets) ** 2).mean()
+        loss.backward()
+        return loss.item(), scales.grad, nu.grad
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize(dev)
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            loss, gs, gn = one()
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    line = {
+        "metric": "surrogate-gradient evaluations/s (10% microcircuit, 200 ms, rate MSE, "
+                  "1 GB300)",
+        "value": args.steps / total, "unit": "gradients/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "10%% microcircuit (7,717 neurons), %d time steps, checkpoints "
+                               "every %d steps, gradient w.r.t. 64 projection scales and nu"
+                               % (n_steps, every),
+                   "l2": "not flushed; wall-clock per gradient including host marshalling"},
+        "loss": loss, "grad_abs_max": float(gs.abs().max()), "grad_nu": float(gn),
+        "clocks": clk.summary(),
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -311,9 +466,16 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4000)
     ap.add_argument("--ref-chunk", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="full", choices=["full", "scale4", "batch", "grad"])
     args = ap.parse_args()
+    if args.workload == "scale4":
+        args.scale = 4.0
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "grad":
+        run_grad(args)
     else:
         run_ours(args)
 

@@ -86,6 +86,7 @@ namespace {
 
 constexpr int kAdjThreads = 512;
 constexpr int kAdjWarps = kAdjThreads / 32;
+constexpr int kAdjUnroll = 8;           // row words per lane in flight
 
 struct AdjParams {
     int32_t n, n_pop, len, chunk;
@@ -128,12 +129,16 @@ __device__ __forceinline__ float surrogate_slope(float x) {
 // the membrane phase; one grid barrier per step separates the lI writes of
 // step t from the row gathers of step t - 1.
 __global__ void __launch_bounds__(kAdjThreads, 1) k_adjoint(const __grid_constant__ AdjParams p) {
-    extern __shared__ float s_ds[];                   // [chunk]
+    // dynamic shared memory: row starts of the CTA's rows [chunk + 1] (u64),
+    // then the spike adjoints of the current step [chunk]
+    extern __shared__ unsigned long long s_rs[];
+    float* s_ds = reinterpret_cast<float*>(s_rs + p.chunk + 1);
     __shared__ volatile uint32_t s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t lo = min(p.n, (int32_t)blockIdx.x * p.chunk);
     const int32_t hi = min(p.n, lo + p.chunk);
     if (tid == 0) s_abort = 0u;
+    for (int32_t j = lo + tid; j <= hi; j += kAdjThreads) s_rs[j - lo] = p.row_start[j];
     __syncthreads();
     const size_t n = (size_t)p.n;
     uint32_t gen = 0;
@@ -153,23 +158,40 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adjoint(const __grid_constan
             float pa[kMaxPop];
 #pragma unroll
             for (int k = 0; k < kMaxPop; ++k) pa[k] = 0.f;
-            const unsigned long long b = p.row_start[j], e = p.row_start[j + 1];
-            for (unsigned long long w = b + lane; w < e; w += 32) {
-                const uint32_t word = __ldg(&p.words[w]);
-                const int32_t tgt = (int32_t)(word & kTgtMask);
-                int pp = 0;
+            const unsigned long long b = s_rs[j - lo], e = s_rs[j - lo + 1];
+            // kAdjUnroll words per lane in flight: all word loads, then all
+            // lI and weight loads, then the (fixed-order) accumulation
+            for (unsigned long long base = b + lane; base < e; base += 32ull * kAdjUnroll) {
+                uint32_t word[kAdjUnroll];
 #pragma unroll
-                for (int k = 1; k < kMaxPop; ++k) pp += tgt >= ps[k] ? 1 : 0;
-                const int code = (int)(word >> 25);
-                const uint32_t slot = (uint32_t)(t + ((word >> kTgtBits) & 63u)) & (kRing - 1);
-                const float l = __ldcg(&p.lring[(size_t)slot * n + tgt]);
-                const float wt = __fmul_rn(__int2float_rn(__ldg(&wq[pp * (kMaxPop * kWCodes) + code])),
-                                           0.00390625f);
-                acc = __fadd_rn(acc, __fmul_rn(wt, l));
-                if (spk) {
-                    const float v = __fmul_rn(__ldg(&bq[pp * (kMaxPop * kWCodes) + code]), l);
+                for (int u = 0; u < kAdjUnroll; ++u) {
+                    const unsigned long long w = base + 32ull * u;
+                    word[u] = w < e ? __ldg(&p.words[w]) : 0u;
+                }
+                float l[kAdjUnroll];
+                int idx[kAdjUnroll];
 #pragma unroll
-                    for (int k = 0; k < kMaxPop; ++k) pa[k] = __fadd_rn(pa[k], k == pp ? v : 0.f);
+                for (int u = 0; u < kAdjUnroll; ++u) {
+                    const int32_t tgt = (int32_t)(word[u] & kTgtMask);
+                    int pp = 0;
+#pragma unroll
+                    for (int k = 1; k < kMaxPop; ++k) pp += tgt >= ps[k] ? 1 : 0;
+                    idx[u] = pp * (kMaxPop * kWCodes) + (int)(word[u] >> 25);
+                    const uint32_t slot = (uint32_t)(t + ((word[u] >> kTgtBits) & 63u)) & (kRing - 1);
+                    l[u] = base + 32ull * u < e ? __ldcg(&p.lring[(size_t)slot * n + tgt]) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < kAdjUnroll; ++u) {
+                    if (base + 32ull * u < e) {
+                        const float wt = __fmul_rn(__int2float_rn(__ldg(&wq[idx[u]])), 0.00390625f);
+                        acc = __fadd_rn(acc, __fmul_rn(wt, l[u]));
+                        if (spk) {
+                            const float v = __fmul_rn(__ldg(&bq[idx[u]]), l[u]);
+                            const int pp = idx[u] / (kMaxPop * kWCodes);
+#pragma unroll
+                            for (int k = 0; k < kMaxPop; ++k) pa[k] = __fadd_rn(pa[k], k == pp ? v : 0.f);
+                        }
+                    }
                 }
             }
             acc = warp_sum(acc);
@@ -477,7 +499,7 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
     ap.barrier = g->sync;
     ap.status = g->sync + 1;
     ap.abort_flag = g->sync + 2;
-    const size_t smem = sizeof(float) * (size_t)ap.chunk;
+    const size_t smem = sizeof(unsigned long long) * ((size_t)ap.chunk + 1) + sizeof(float) * (size_t)ap.chunk;
     GCK(cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
 
     StepParams sp;
