@@ -211,7 +211,8 @@ def run_ours(args):
     for _ in range(args.warmup):
         net.step(chunk)
     net.sync()
-    net.read_spikes_into(np.zeros(1 << 22, np.uint32), np.zeros(1 << 22, np.uint32))
+    n_pending = max(1, net.raster_size())
+    net.read_spikes_into(np.zeros(n_pending, np.uint32), np.zeros(n_pending, np.uint32))
 
     # -------- device-timed region: K launches, inputs (1.2 GB rows) > L2 --------
     c0 = net.counters()
@@ -381,7 +382,7 @@ def run_batch(args):
                                % (info["n_neurons_total"], info["graph_steps"], chunk),
                    "time_steps_per_step": chunk, "instances": len(b),
                    "tilings": {"warp_per_spike": tilings.count(0),
-                               "block_per_row": tilings.count(1)},
+                               "block_per_row": tilings.count(1), "flat": tilings.count(2)},
                    "l2": "no flush: the 64 instances' synapse rows and ring buffers exceed L2",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "us_per_time_step": total_ms * 1e3 / (args.steps * chunk),

@@ -315,8 +315,10 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
  *
  * Delivery tiling per instance: at creation an autotuner times, on each
  * instance's own rows and a spike list of the size its activity gives (about
- * 5 Hz x N x 0.1 ms), one warp per spike (tiling 0) against one CTA per row
- * (tiling 1), and keeps the faster; snn_batch_get_info reports both times.
+ * 5 Hz x N x 0.1 ms), one warp per spike (tiling 0), one CTA per row
+ * (tiling 1) and flat (tiling 2: the rows of all flat-tiled spikes of a step
+ * concatenated and spread over every warp of the grid), and keeps the
+ * fastest; snn_batch_get_info reports the three times.
  *
  * Steps are issued as replays of one captured CUDA graph of 1000 steps; the
  * kernel reads its first step index from device memory and advances it, so
@@ -331,9 +333,10 @@ typedef struct snn_batch_info {
     int32_t n_neurons_total;     /* concatenated neurons of all instances */
     int32_t n_neurons;           /* of the queried instance */
     int64_t n_synapses;          /* of the queried instance */
-    int32_t tiling;              /* 0 warp per spike, 1 CTA per row */
+    int32_t tiling;              /* 0 warp per spike, 1 CTA per row, 2 flat */
     float tune_us_warp;          /* autotuner probe times, microseconds */
     float tune_us_block;
+    float tune_us_flat;
     int32_t blocks, threads, neurons_per_thread;
     int32_t graph;               /* 1 if the graph was captured */
     int32_t graph_steps;         /* steps per graph replay */
@@ -382,7 +385,7 @@ int snn_batch_counters(snn_batch* b, int32_t k, int64_t* step, uint64_t* spikes,
 int snn_batch_get_info(snn_batch* b, int32_t k, snn_batch_info* info);
 
 /* snn_batch_set_tiling -- override the autotuner's delivery tiling of
- * instance k (0 one warp per spike, 1 one CTA per row) for the steps issued
+ * instance k (0 one warp per spike, 1 one CTA per row, 2 flat) for the steps issued
  * after the call.  Results do not depend on the tiling.  Synchronises. */
 int snn_batch_set_tiling(snn_batch* b, int32_t k, int32_t tiling);
 

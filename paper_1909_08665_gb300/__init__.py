@@ -90,6 +90,7 @@ class SnnBatchInfo(C.Structure):
     _fields_ = [("n_instances", C.c_int32), ("n_neurons_total", C.c_int32),
                 ("n_neurons", C.c_int32), ("n_synapses", C.c_int64), ("tiling", C.c_int32),
                 ("tune_us_warp", C.c_float), ("tune_us_block", C.c_float),
+                ("tune_us_flat", C.c_float),
                 ("blocks", C.c_int32), ("threads", C.c_int32),
                 ("neurons_per_thread", C.c_int32), ("graph", C.c_int32),
                 ("graph_steps", C.c_int32)]

@@ -5,7 +5,7 @@
 //
 // The neurons of all instances are concatenated: instance k owns the global
 // range [goff_k, goff_k + n_k).  CTA b owns the contiguous range
-// [b * 512 * NPT, (b + 1) * 512 * NPT) and keeps u, I and the refractory
+// [b * chunk, (b + 1) * chunk), chunk = ceil(total / CTAs) <= 512 NPT, and keeps u, I and the refractory
 // counter of its neurons in registers; the four cached background draws of
 // each neuron sit in shared memory.  The 64-slot ring buffers of all neurons
 // are one global array [slot][global neuron].
@@ -23,10 +23,14 @@
 // Every result equals the single-network path bit for bit (same fp32
 // operation order, integer accumulation, same random counters).
 //
-// Delivery tiling per instance: one warp per spike (tiling 0) or one CTA per
-// row (tiling 1).  The autotuner (host side, at creation) times both on each
-// instance's own rows with a seeded spike list of the instance's expected
-// size and keeps the faster one.
+// Delivery tiling per instance: one warp per spike (tiling 0), one CTA per
+// row (tiling 1), or flat (tiling 2): every CTA stages the step's flat-list
+// rows (start, length, instance) in shared memory with a block scan, and all
+// warps of the grid stride over the concatenated words, so one row's latency
+// chain is paid once per step and the work is spread evenly over the SMs.
+// The autotuner (host side, at creation) times the three on each instance's
+// own rows with a seeded spike list of the instance's expected size and keeps
+// the fastest.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -51,6 +55,9 @@ constexpr int kMaxInst = 1024;
 constexpr int kGraphChunk = 1000;       // steps per captured launch
 constexpr int kWarpUnroll = 8;          // words in flight per lane, warp tiling
 constexpr int kBlockUnroll = 4;         // words in flight per thread, CTA tiling
+constexpr int kFlatUnroll = 4;          // words in flight per lane, flat tiling
+constexpr int kFlatChunk = 1024;        // flat-list rows staged at once
+constexpr int kTilings = 3;
 constexpr uint32_t kBatchRasterOverflow = 2u;
 
 // per-instance constants read in the neuron phases (one 48-byte record)
@@ -71,6 +78,7 @@ struct InstCold {
 
 struct BatchParams {
     int32_t n_inst, ntot, n_steps;
+    int32_t chunk;                      // neurons per CTA (<= NPT * kBThreads)
     int32_t inject_fault;               // 1: CTA 0 never arrives at a barrier
     uint64_t timeout_ns;
     const InstHot* hot;
@@ -78,12 +86,14 @@ struct BatchParams {
     const uint32_t* pois;               // [n_inst][8][32] thresholds minus one
     const float* cdc;                   // [n_inst][8] P20 * I_DC
     const int32_t* goff;                // [n_inst + 1]
+    const int32_t* wtab_all;            // [n_inst][8][8][128] fixed-point weights
+    const int32_t* ps_all;              // [n_inst][8] population starts (unused: INT_MAX)
     float* u;
     float* i_syn;
     int32_t* refr;
     int32_t* ring;                      // [64][ntot]
-    uint32_t* list;                     // [2 parity][2 tiling][ntot] global ids
-    uint32_t* cnt;                      // [4 parity][2 tiling]
+    uint32_t* list;                     // [2 parity][3 tiling][ntot] global ids
+    uint32_t* cnt;                      // [4 parity][3 tiling]
     uint32_t* ras_step;
     uint32_t* ras_id;
     uint32_t* ras_n;
@@ -154,16 +164,144 @@ __device__ __forceinline__ void deliver_row(const BatchParams& p, const int32_t*
     if (count && r == 0) atomicAdd(&p.inst_counters[ki * 2 + 1], e - b);
 }
 
+// shared-memory arrays of the flat tiling (after the caller's own arrays)
+struct FlatSmem {
+    int32_t* ps;                 // [n_inst][8] population starts
+    const uint32_t** beg;        // [kFlatChunk] first word of each staged row
+    uint32_t* pre;               // [kFlatChunk + 1] exclusive prefix of row lengths
+    uint32_t* meta;              // [kFlatChunk] instance << 3 | source population
+    uint32_t* wsum;              // [kBWarps] scan partials
+};
+
+__host__ __device__ inline size_t flat_smem_bytes(int n_inst) {
+    return (size_t)kFlatChunk * sizeof(void*) + (size_t)n_inst * 8 * sizeof(int32_t) +
+           ((size_t)kFlatChunk + 1) * 4 + (size_t)kFlatChunk * 4 + kBWarps * 4;
+}
+
+__device__ inline FlatSmem flat_smem(unsigned char* base, int n_inst) {
+    FlatSmem F;
+    F.beg = reinterpret_cast<const uint32_t**>(base);
+    F.ps = reinterpret_cast<int32_t*>(base + (size_t)kFlatChunk * sizeof(void*));
+    F.pre = reinterpret_cast<uint32_t*>(F.ps + (size_t)n_inst * 8);
+    F.meta = F.pre + kFlatChunk + 1;
+    F.wsum = F.meta + kFlatChunk;
+    return F;
+}
+
+__device__ inline void flat_load_ps(const BatchParams& p, const FlatSmem& F) {
+    for (int k = threadIdx.x; k < p.n_inst * 8; k += kBThreads) F.ps[k] = __ldg(&p.ps_all[k]);
+}
+
+// Flat tiling: the rows of the nf spikes in `list`, spread over every warp of
+// the grid.  Every CTA stages the same rows; CTA 0 alone counts the events.
+__device__ void deliver_flat(const BatchParams& p, const int32_t* s_goff, const FlatSmem& F,
+                             const uint32_t* list, uint32_t nf, long long t, bool count) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t ntot = (size_t)p.ntot;
+    for (uint32_t f0 = 0; f0 < nf; f0 += kFlatChunk) {
+        const uint32_t mc = min((uint32_t)kFlatChunk, nf - f0);
+        // stage two rows per thread: start, length, instance and population
+        uint32_t len[2] = {0u, 0u};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t k = (uint32_t)tid * 2u + (uint32_t)h;
+            if (k < mc) {
+                const int32_t gi = (int32_t)__ldcg(&list[f0 + k]);
+                const int ki = inst_of(s_goff, p.n_inst, gi);
+                const int32_t j = gi - s_goff[ki];
+                int q = 0;
+#pragma unroll
+                for (int m = 1; m < kMaxPop; ++m) q += j >= F.ps[ki * 8 + m] ? 1 : 0;
+                const InstCold& I = p.cold[ki];
+                const unsigned long long b = I.row_start[j], e = I.row_start[j + 1];
+                F.beg[k] = I.words + b;
+                F.meta[k] = ((uint32_t)ki << 3) | (uint32_t)q;
+                len[h] = (uint32_t)(e - b);
+                if (count && blockIdx.x == 0) atomicAdd(&p.inst_counters[ki * 2 + 1], e - b);
+            }
+        }
+        // exclusive prefix of the row lengths (block scan)
+        const uint32_t v = len[0] + len[1];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) F.wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w0 = lane < kBWarps ? F.wsum[lane] : 0u;
+            uint32_t z = w0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+                if (lane >= o) z += y;
+            }
+            if (lane < kBWarps) F.wsum[lane] = z - w0;
+        }
+        __syncthreads();
+        const uint32_t excl = F.wsum[warp] + x - v;
+        if ((uint32_t)tid * 2u < mc) F.pre[tid * 2] = excl;
+        if ((uint32_t)tid * 2u + 1u < mc) F.pre[tid * 2 + 1] = excl + len[0];
+        if (tid == kBThreads - 1) F.pre[mc] = excl + v;
+        __syncthreads();
+        const uint32_t W = F.pre[mc];
+        // words: chunks of 32 kFlatUnroll per warp, interleaved over the SMs
+        const uint32_t gw = (uint32_t)warp * gridDim.x + blockIdx.x;
+        const uint32_t step_w = (uint32_t)kBWarps * gridDim.x * 32u * kFlatUnroll;
+        for (uint32_t c0 = gw * 32u * kFlatUnroll; c0 < W; c0 += step_w) {
+            uint32_t word[kFlatUnroll], meta[kFlatUnroll];
+#pragma unroll
+            for (int u = 0; u < kFlatUnroll; ++u) {
+                const uint32_t w = c0 + (uint32_t)u * 32u + (uint32_t)lane;
+                word[u] = 0u;
+                meta[u] = 0xffffffffu;
+                if (w < W) {
+                    uint32_t lo = 0u, hi = mc;          // pre[lo] <= w < pre[hi]
+                    while (hi - lo > 1u) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (F.pre[mid] <= w) lo = mid;
+                        else hi = mid;
+                    }
+                    word[u] = __ldg(F.beg[lo] + (w - F.pre[lo]));
+                    meta[u] = F.meta[lo];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kFlatUnroll; ++u) {
+                if (meta[u] != 0xffffffffu) {
+                    const int ki = (int)(meta[u] >> 3), q = (int)(meta[u] & 7u);
+                    const int32_t tgt = (int32_t)(word[u] & kTgtMask);
+                    int pp = 0;
+#pragma unroll
+                    for (int m = 1; m < kMaxPop; ++m) pp += tgt >= F.ps[ki * 8 + m] ? 1 : 0;
+                    const int32_t wt = __ldg(&p.wtab_all[(((size_t)ki * kMaxPop + pp) * kMaxPop + q) *
+                                                         kWCodes + (word[u] >> 25)]);
+                    const uint32_t slot = (uint32_t)(t + ((word[u] >> kTgtBits) & 63u)) & (kRing - 1);
+                    atomicAdd(&p.ring[(size_t)slot * ntot + s_goff[ki] + tgt], wt);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <int NPT>
 __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ BatchParams p) {
-    extern __shared__ uint32_t s_rnd[];            // [NPT][4 draws][kBThreads]
+    // dynamic shared memory: the cached background draws [NPT][4][kBThreads],
+    // then the flat tiling's arrays
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    uint32_t* s_rnd = reinterpret_cast<uint32_t*>(s_dyn);
+    const FlatSmem F = flat_smem(s_dyn + (size_t)NPT * 4 * kBThreads * sizeof(uint32_t), p.n_inst);
     __shared__ int32_t s_goff[kMaxInst + 1];
     __shared__ volatile uint32_t s_abort;
     const int tid = threadIdx.x, lane = tid & 31;
     for (int k = tid; k <= p.n_inst; k += kBThreads) s_goff[k] = p.goff[k];
+    flat_load_ps(p, F);
     if (tid == 0) s_abort = 0u;
     __syncthreads();
-    const int32_t gbase = (int32_t)blockIdx.x * (kBThreads * NPT) + tid;
+    const int32_t gbase = (int32_t)blockIdx.x * p.chunk + tid;
     const long long t0 = *p.step;
     const int n = p.n_steps;
     const size_t ntot = (size_t)p.ntot;
@@ -174,7 +312,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ 
     for (int k = 0; k < NPT; ++k) {
         const int32_t gi = gbase + k * kBThreads;
         u[k] = 0.f; isyn[k] = 0.f; refr[k] = 0; ip[k] = -1;
-        if (gi < p.ntot) {
+        if (k * kBThreads + tid < p.chunk && gi < p.ntot) {
             u[k] = p.u[gi];
             isyn[k] = p.i_syn[gi];
             refr[k] = p.refr[gi];
@@ -224,22 +362,25 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ 
             }
             const unsigned m = __ballot_sync(0xffffffffu, spk);
             if (m) {
-                const unsigned mb = __ballot_sync(0xffffffffu, spk && tiling == 1);
-                const unsigned mw = m & ~mb;
-                uint32_t bw = 0, bb = 0, br = 0;
+                unsigned mt[kTilings];
+                mt[1] = __ballot_sync(0xffffffffu, spk && tiling == 1);
+                mt[2] = __ballot_sync(0xffffffffu, spk && tiling == 2);
+                mt[0] = m & ~mt[1] & ~mt[2];
+                uint32_t bt[kTilings] = {0u, 0u, 0u}, br = 0;
                 if (lane == 0) {
-                    if (mw) bw = atomicAdd(&p.cnt[par4 * 2 + 0], (uint32_t)__popc(mw));
-                    if (mb) bb = atomicAdd(&p.cnt[par4 * 2 + 1], (uint32_t)__popc(mb));
+#pragma unroll
+                    for (int tl = 0; tl < kTilings; ++tl)
+                        if (mt[tl]) bt[tl] = atomicAdd(&p.cnt[par4 * kTilings + tl], (uint32_t)__popc(mt[tl]));
                     br = atomicAdd(p.ras_n, (uint32_t)__popc(m));
                 }
-                bw = __shfl_sync(0xffffffffu, bw, 0);
-                bb = __shfl_sync(0xffffffffu, bb, 0);
+#pragma unroll
+                for (int tl = 0; tl < kTilings; ++tl) bt[tl] = __shfl_sync(0xffffffffu, bt[tl], 0);
                 br = __shfl_sync(0xffffffffu, br, 0);
                 if (spk) {
                     const unsigned lt = (1u << lane) - 1u;
-                    const uint32_t pos = tiling ? bb + (uint32_t)__popc(mb & lt)
-                                                : bw + (uint32_t)__popc(mw & lt);
-                    p.list[((size_t)par2 * 2 + (uint32_t)tiling) * ntot + pos] = (uint32_t)gi;
+                    const uint32_t pos = (tiling == 0 ? bt[0] : tiling == 1 ? bt[1] : bt[2]) +
+                                         (uint32_t)__popc((tiling == 0 ? mt[0] : tiling == 1 ? mt[1] : mt[2]) & lt);
+                    p.list[((size_t)par2 * kTilings + (uint32_t)tiling) * ntot + pos] = (uint32_t)gi;
                     const uint32_t rp = br + (uint32_t)__popc(m & lt);
                     if (rp < p.ras_cap) {
                         p.ras_step[rp] = (uint32_t)t;
@@ -259,15 +400,18 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ 
         const long long t = t0 + s;
         if (!grid_sync(p, gen, &s_abort)) break;
         // counters of step t + 2: last read in D(t - 2), next written in A(t + 2)
-        if (blockIdx.x == 0 && tid < 2) p.cnt[(uint32_t)((t + 2) & 3) * 2 + tid] = 0u;
+        if (blockIdx.x == 0 && tid < kTilings) p.cnt[(uint32_t)((t + 2) & 3) * kTilings + tid] = 0u;
 
         // ---- D(t): spikes of step t ----
         {
             const uint32_t par4 = (uint32_t)(t & 3), par2 = (uint32_t)(t & 1);
-            const uint32_t nw = __ldcg(&p.cnt[par4 * 2 + 0]);
-            const uint32_t nb = __ldcg(&p.cnt[par4 * 2 + 1]);
-            const uint32_t* lw = p.list + ((size_t)par2 * 2 + 0) * ntot;
-            const uint32_t* lb = p.list + ((size_t)par2 * 2 + 1) * ntot;
+            const uint32_t nw = __ldcg(&p.cnt[par4 * kTilings + 0]);
+            const uint32_t nb = __ldcg(&p.cnt[par4 * kTilings + 1]);
+            const uint32_t nf = __ldcg(&p.cnt[par4 * kTilings + 2]);
+            const uint32_t* lw = p.list + ((size_t)par2 * kTilings + 0) * ntot;
+            const uint32_t* lb = p.list + ((size_t)par2 * kTilings + 1) * ntot;
+            const uint32_t* lf = p.list + ((size_t)par2 * kTilings + 2) * ntot;
+            if (nf) deliver_flat(p, s_goff, F, lf, nf, t, true);
             // warp w of CTA b takes spikes w * grid + b, spreading them over SMs
             for (uint32_t k = (uint32_t)(tid >> 5) * gridDim.x + blockIdx.x; k < nw;
                  k += (uint32_t)kBWarps * gridDim.x)
@@ -341,11 +485,16 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ 
 __global__ void __launch_bounds__(kBThreads) k_probe_deliver(const __grid_constant__ BatchParams p,
                                                              const uint32_t* spikes, int n,
                                                              int tiling) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    const FlatSmem F = flat_smem(s_dyn, p.n_inst);
     __shared__ int32_t s_goff[kMaxInst + 1];
     for (int k = threadIdx.x; k <= p.n_inst; k += kBThreads) s_goff[k] = p.goff[k];
+    flat_load_ps(p, F);
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    if (tiling == 0) {
+    if (tiling == 2) {
+        deliver_flat(p, s_goff, F, spikes, (uint32_t)n, 0, false);
+    } else if (tiling == 0) {
         const int warps = (int)gridDim.x * kBWarps;
         for (int k = (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x; k < n; k += warps)
             deliver_row<kWarpUnroll>(p, s_goff, (int32_t)spikes[k], 0, lane, 32, false);
@@ -373,7 +522,9 @@ const void* select_batch(int npt) {
     }
 }
 
-size_t batch_smem(int npt) { return (size_t)npt * 4 * kBThreads * sizeof(uint32_t); }
+size_t batch_smem(int npt, int n_inst) {
+    return (size_t)npt * 4 * kBThreads * sizeof(uint32_t) + flat_smem_bytes(n_inst);
+}
 
 }  // namespace
 }  // namespace snn
@@ -391,10 +542,11 @@ struct snn_batch {
     std::vector<InstHot> hot_h;
     std::vector<InstCold> cold_h;
     std::vector<uint64_t> nnz;
-    std::vector<float> tune_us[2];
+    std::vector<float> tune_us[kTilings];
     std::vector<unsigned long long*> row_start;
     std::vector<uint32_t*> words;
-    std::vector<int32_t*> wtab;
+    int32_t* d_wtab_all = nullptr;       // [n_inst][8][8][128]
+    int32_t* d_ps_all = nullptr;         // [n_inst][8]
     BatchParams p;
     InstHot* d_hot = nullptr;
     InstCold* d_cold = nullptr;
@@ -449,8 +601,7 @@ void free_batch(snn_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (auto* x : b->row_start) cudaFree(x);
     for (auto* x : b->words) cudaFree(x);
-    for (auto* x : b->wtab) cudaFree(x);
-    void* ptrs[] = {b->d_hot, b->d_cold, b->d_pois, b->d_cdc, b->d_goff, b->d_u, b->d_i,
+    void* ptrs[] = {b->d_wtab_all, b->d_ps_all, b->d_hot, b->d_cold, b->d_pois, b->d_cdc, b->d_goff, b->d_u, b->d_i,
                     b->d_r, b->d_ring, b->d_list, b->d_cnt, b->d_ras_step, b->d_ras_id,
                     b->d_ras_n, b->d_ic, b->d_step, b->d_sync};
     for (void* x : ptrs)
@@ -487,8 +638,8 @@ int autotune(snn_batch* b) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    b->tune_us[0].assign(b->n_inst, 0.f);
-    b->tune_us[1].assign(b->n_inst, 0.f);
+    for (int tl = 0; tl < kTilings; ++tl) b->tune_us[tl].assign(b->n_inst, 0.f);
+    const size_t probe_smem = flat_smem_bytes(b->n_inst);
     for (int k = 0; k < b->n_inst && e == cudaSuccess; ++k) {
         const InstCold& I = b->cold_h[k];
         // about 5 Hz of activity in one 0.1 ms step, at least 4 spikes
@@ -502,13 +653,14 @@ int autotune(snn_batch* b) {
             spk[i] = (uint32_t)(I.goff + (int)((x * 0x2545F4914F6CDD1Dull) % (uint64_t)I.n));
         }
         e = cudaMemcpyAsync(d_spk, spk.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s);
-        for (int tl = 0; tl < 2 && e == cudaSuccess; ++tl) {
-            const int grid = tl == 0 ? std::min(b->blocks, std::max(1, (n + kBWarps - 1) / kBWarps))
-                                     : std::min(b->blocks, n);
+        for (int tl = 0; tl < kTilings && e == cudaSuccess; ++tl) {
+            const int grid = tl == 0   ? std::min(b->blocks, std::max(1, (n + kBWarps - 1) / kBWarps))
+                             : tl == 1 ? std::min(b->blocks, n)
+                                       : b->blocks;
             float best = 1e30f;
             for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
                 cudaEventRecord(e0, s);
-                k_probe_deliver<<<grid, kBThreads, 0, s>>>(b->p, d_spk, n, tl);
+                k_probe_deliver<<<grid, kBThreads, probe_smem, s>>>(b->p, d_spk, n, tl);
                 cudaEventRecord(e1, s);
                 e = cudaEventSynchronize(e1);
                 float ms = 0.f;
@@ -517,7 +669,10 @@ int autotune(snn_batch* b) {
             }
             b->tune_us[tl][k] = best * 1000.f;
         }
-        b->hot_h[k].key.z = b->tune_us[1][k] < b->tune_us[0][k] ? 1u : 0u;
+        uint32_t best_tl = 0;
+        for (int tl = 1; tl < kTilings; ++tl)
+            if (b->tune_us[tl][k] < b->tune_us[best_tl][k]) best_tl = (uint32_t)tl;
+        b->hot_h[k].key.z = best_tl;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -579,6 +734,8 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
     b->host_ids.resize(n_inst);
     std::vector<uint32_t> pois((size_t)n_inst * kMaxPop * kPoisTable, 0xffffffffu);
     std::vector<float> cdc((size_t)n_inst * kMaxPop, 0.f);
+    std::vector<int32_t> wtab_all((size_t)n_inst * kMaxPop * kMaxPop * kWCodes);
+    std::vector<int32_t> ps_all((size_t)n_inst * 8);
     int rc = SNN_OK;
     long long ntot = 0;
     for (int k = 0; k < n_inst && rc == SNN_OK; ++k) {
@@ -610,33 +767,37 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
         b->row_start.push_back(rs);
         b->words.push_back(wd);
         b->nnz[k] = nnz;
-        int32_t* wt = nullptr;
-        rc = balloc(&wt, kMaxPop * kMaxPop * kWCodes, "batch weight table");
-        if (rc != SNN_OK) break;
-        b->wtab.push_back(wt);
-        const cudaError_t ce = cudaMemcpy(wt, ht.wtab, sizeof(ht.wtab), cudaMemcpyHostToDevice);
-        if (ce != cudaSuccess) {
-            rc = set_cuda_error(ce, "weight table upload");
-            break;
-        }
+        std::memcpy(wtab_all.data() + (size_t)k * kMaxPop * kMaxPop * kWCodes, ht.wtab, sizeof(ht.wtab));
+        for (int m = 0; m < 8; ++m)
+            ps_all[(size_t)k * 8 + m] = m == 0 ? 0 : (m < ht.n_pop ? ht.pop_start[m] : 0x7fffffff);
         C.row_start = rs;
         C.words = wd;
-        C.wtab = wt;
         ntot += ht.n;
         b->goff[k + 1] = (int32_t)ntot;
         if (ntot > (1ll << 30)) rc = set_error(SNN_ERR_INVALID, "too many neurons in the batch");
+    }
+    if (rc == SNN_OK) rc = balloc(&b->d_wtab_all, wtab_all.size(), "batch weight tables");
+    if (rc == SNN_OK) rc = balloc(&b->d_ps_all, ps_all.size(), "batch population starts");
+    if (rc == SNN_OK) {
+        const cudaError_t ce = cudaMemcpy(b->d_wtab_all, wtab_all.data(), sizeof(int32_t) * wtab_all.size(),
+                                          cudaMemcpyHostToDevice);
+        const cudaError_t ce2 = cudaMemcpy(b->d_ps_all, ps_all.data(), sizeof(int32_t) * ps_all.size(),
+                                           cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess || ce2 != cudaSuccess) rc = set_error(SNN_ERR_CUDA, "table upload");
     }
     if (rc != SNN_OK) {
         free_batch(b);
         return rc;
     }
+    for (int k = 0; k < n_inst; ++k)
+        b->cold_h[k].wtab = b->d_wtab_all + (size_t)k * kMaxPop * kMaxPop * kWCodes;
     b->ntot = (int)ntot;
     // launch shape: one CTA per SM, the fewest neurons per thread that cover the batch
     b->blocks = prop.multiProcessorCount;
     b->npt = 0;
     for (int npt : kNptVariants) {
         if ((long long)npt * kBThreads * b->blocks < ntot) continue;
-        const size_t smem = batch_smem(npt);
+        const size_t smem = batch_smem(npt, n_inst);
         if (cudaFuncSetAttribute(select_batch(npt), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             break;
@@ -665,8 +826,8 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
     if (rc == SNN_OK) rc = balloc(&b->d_i, ntot, "batch I");
     if (rc == SNN_OK) rc = balloc(&b->d_r, ntot, "batch refractory counters");
     if (rc == SNN_OK) rc = balloc(&b->d_ring, (size_t)kRing * ntot, "batch ring buffers");
-    if (rc == SNN_OK) rc = balloc(&b->d_list, (size_t)4 * ntot, "batch spike lists");
-    if (rc == SNN_OK) rc = balloc(&b->d_cnt, 8, "batch list counters");
+    if (rc == SNN_OK) rc = balloc(&b->d_list, (size_t)2 * kTilings * ntot, "batch spike lists");
+    if (rc == SNN_OK) rc = balloc(&b->d_cnt, 4 * kTilings, "batch list counters");
     if (rc == SNN_OK) rc = balloc(&b->d_ras_step, b->ras_cap, "batch raster");
     if (rc == SNN_OK) rc = balloc(&b->d_ras_id, b->ras_cap, "batch raster");
     if (rc == SNN_OK) rc = balloc(&b->d_ras_n, 1, "batch raster count");
@@ -690,7 +851,7 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_i, 0, sizeof(float) * ntot, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_r, 0, sizeof(int32_t) * ntot, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ring, 0, sizeof(int32_t) * (size_t)kRing * ntot, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cnt, 0, sizeof(uint32_t) * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cnt, 0, sizeof(uint32_t) * 4 * kTilings, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ras_n, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ic, 0, sizeof(unsigned long long) * 2 * n_inst, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step, 0, sizeof(long long), s);
@@ -709,6 +870,7 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
     std::memset(&p, 0, sizeof(p));
     p.n_inst = n_inst;
     p.ntot = b->ntot;
+    p.chunk = (int32_t)(((long long)b->ntot + b->blocks - 1) / b->blocks);
     p.timeout_ns = (uint64_t)(((opt && opt->timeout_s > 0) ? opt->timeout_s : 2.0) * 1e9);
     p.inject_fault = opt ? opt->inject_fault : 0;
     p.hot = b->d_hot;
@@ -716,6 +878,8 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
     p.pois = b->d_pois;
     p.cdc = b->d_cdc;
     p.goff = b->d_goff;
+    p.wtab_all = b->d_wtab_all;
+    p.ps_all = b->d_ps_all;
     p.u = b->d_u;
     p.i_syn = b->d_i;
     p.refr = b->d_r;
@@ -731,6 +895,11 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
     p.barrier = b->d_sync;
     p.status = b->d_sync + 1;
     p.abort_flag = b->d_sync + 2;
+    if (cudaFuncSetAttribute(k_probe_deliver, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)flat_smem_bytes(n_inst)) != cudaSuccess) {
+        free_batch(b);
+        return set_error(SNN_ERR_CUDA, "probe kernel shared memory");
+    }
     rc = autotune(b);
     if (rc != SNN_OK) {
         free_batch(b);
@@ -843,6 +1012,7 @@ int snn_batch_get_info(snn_batch* b, int32_t k, snn_batch_info* info) {
     info->tiling = (int32_t)b->hot_h[k].key.z;
     info->tune_us_warp = b->tune_us[0][k];
     info->tune_us_block = b->tune_us[1][k];
+    info->tune_us_flat = b->tune_us[2][k];
     info->blocks = b->blocks;
     info->threads = kBThreads;
     info->neurons_per_thread = b->npt;
@@ -852,7 +1022,7 @@ int snn_batch_get_info(snn_batch* b, int32_t k, snn_batch_info* info) {
 }
 
 int snn_batch_set_tiling(snn_batch* b, int32_t k, int32_t tiling) {
-    if (!b || k < 0 || k >= b->n_inst || (tiling != 0 && tiling != 1))
+    if (!b || k < 0 || k >= b->n_inst || tiling < 0 || tiling >= kTilings)
         return set_error(SNN_ERR_INVALID, "bad arguments");
     b->hot_h[k].key.z = (uint32_t)tiling;
     BCK(cudaMemcpyAsync(b->d_hot + k, &b->hot_h[k], sizeof(InstHot), cudaMemcpyHostToDevice,

@@ -160,17 +160,22 @@ k_seg_from_rows(const unsigned long long* row_start, const uint32_t* words,
 }
 
 // longest segment (words of one row that target one partition)
+// longest (row, partition) segment of each partition: one CTA per partition
 __global__ void k_max_segment(const uint32_t* seg, int n, int n_part, uint32_t* out) {
+    __shared__ uint32_t red[kBuildThreads / 32];
+    const int c = blockIdx.x;
     uint32_t m = 0;
-    const size_t total = (size_t)n * n_part;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (size_t)gridDim.x * blockDim.x) {
-        const size_t j = k / n_part, c = k % n_part;
-        const uint32_t* r = seg + j * (n_part + 1) + c;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const uint32_t* r = seg + (size_t)j * (n_part + 1) + c;
         m = max(m, r[1] - r[0]);
     }
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
+        out[c] = m;
+    }
 }
 
 // Partition slots: slot (j, c) is a run of 8-byte entries; entry 0 holds the
@@ -178,12 +183,13 @@ __global__ void k_max_segment(const uint32_t* seg, int n, int n_part, uint32_t* 
 // synapses ready for accumulation: the fixed-point weight
 // wtab[pop(i)][pop(j)][code] and the ring offset delay * ncmax + (i - part_lo[c]).
 // The step kernel adds the weight at ((t mod 64) * ncmax + offset) mod (64 ncmax).
-// Slots are partition-major (slot (j, c) at (c * n + j) * slot_entries), so
+// Slots are partition-major: slot (j, c) starts at slot_base[c] + j * S_c,
+// where S_c (a power of two, >= 32) exceeds partition c's longest segment, so
 // one partition's slots form one contiguous region.  One warp per (j, c).
 __global__ void __launch_bounds__(kBuildThreads)
 k_build_slots(const uint32_t* words, const uint32_t* seg, const int32_t* part_lo,
               const int32_t* wtab, int n, int n_part, int n_pop, SlotPops pops, int ncmax,
-              int slot_entries, int2* slots) {
+              const unsigned long long* slot_base, const uint32_t* slot_S, int2* slots) {
     const size_t warp_id = ((size_t)blockIdx.x * kBuildThreads + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp_id >= (size_t)n * n_part) return;
@@ -193,7 +199,7 @@ k_build_slots(const uint32_t* words, const uint32_t* seg, const int32_t* part_lo
     const uint32_t* r = seg + j * (n_part + 1) + c;
     const uint32_t b = r[0], e = r[1];
     const int32_t lo = part_lo[c];
-    int2* out = slots + ((size_t)c * (size_t)n + j) * (size_t)slot_entries;
+    int2* out = slots + slot_base[c] + j * (size_t)slot_S[c];
     if (lane == 0) out[0] = make_int2((int)(e - b), 0);
     for (uint32_t k = b + lane; k < e; k += 32) {
         const uint32_t w = words[k];
@@ -236,22 +242,22 @@ cudaError_t launch_build_fill(const BuildParams& bp, const unsigned long long* r
 
 cudaError_t launch_max_segment(const uint32_t* seg, int n, int n_part, uint32_t* out,
                                cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
-    k_max_segment<<<1024, 256, 0, s>>>(seg, n, n_part, out);
+    k_max_segment<<<n_part, kBuildThreads, 0, s>>>(seg, n, n_part, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_build_slots(const uint32_t* words, const uint32_t* seg, const int32_t* part_lo,
                                const int32_t* wtab, int n, int n_part, int n_pop,
-                               const int32_t* pop_start, int ncmax, int slot_entries, int2* slots,
-                               cudaStream_t s) {
+                               const int32_t* pop_start, int ncmax,
+                               const unsigned long long* slot_base, const uint32_t* slot_S,
+                               int2* slots, cudaStream_t s) {
     SlotPops pops;
     for (int p = 0; p <= kMaxPop; ++p) pops.pop_start[p] = pop_start[p];
     const size_t warps = (size_t)n * n_part;
     const size_t blocks = (warps * 32 + kBuildThreads - 1) / kBuildThreads;
     k_build_slots<<<(unsigned)blocks, kBuildThreads, 0, s>>>(words, seg, part_lo, wtab, n, n_part,
-                                                            n_pop, pops, ncmax, slot_entries, slots);
+                                                            n_pop, pops, ncmax, slot_base, slot_S,
+                                                            slots);
     return cudaGetLastError();
 }
 

@@ -186,6 +186,7 @@ void free_net(snn_net* net) {
     if (!net) return;
     void* ptrs[] = {net->d_part_lo, net->d_row_start, net->d_seg, net->d_words, net->d_wtab,
                     net->d_dtab, net->d_u, net->d_i, net->d_r, net->d_ring, net->d_msg, net->d_slots,
+                    net->d_slot_base, net->d_slot_S,
                     net->d_ras_step, net->d_ras_id, net->d_ras_n,
                     net->d_counters, net->d_sync, net->d_pop_spikes};
     for (void* p : ptrs)
@@ -320,21 +321,41 @@ int finish_network(snn_net* net) {
     cudaStream_t s = net->stream;
     CALL(dalloc(&net->d_wtab, kMaxPop * kMaxPop * kWCodes, "wtab"));
     CK(cudaMemcpyAsync(net->d_wtab, net->wtab, sizeof(net->wtab), cudaMemcpyHostToDevice, s));
+    // per partition c: S_c = power of two >= its longest segment + 1 (entry 0
+    // is the count), at least 32; partition c's slots start at base_c
+    const int P = net->P;
     uint32_t* d_max = nullptr;
-    CALL(dalloc(&d_max, 1, "segment maximum"));
-    uint32_t lmax = 0;
-    cudaError_t e = launch_max_segment(net->d_seg, net->n, net->P, d_max, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&lmax, d_max, sizeof(lmax), cudaMemcpyDeviceToHost, s);
+    CALL(dalloc(&d_max, P, "segment maxima"));
+    std::vector<uint32_t> lmax(P, 0);
+    cudaError_t e = launch_max_segment(net->d_seg, net->n, P, d_max, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(lmax.data(), d_max, sizeof(uint32_t) * P, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_max);
-    if (e != cudaSuccess) return cuda_fail(e, "segment maximum");
-    int se = 32;
-    while (se < (int)lmax + 1) se *= 2;
-    net->slot_entries = se;
-    // + 2 entries of tail padding, like every array a bulk prefetch covers
-    CALL(dalloc(&net->d_slots, (size_t)net->n * net->P * se + 2, "partition slots"));
-    CK(launch_build_slots(net->d_words, net->d_seg, net->d_part_lo, net->d_wtab, net->n, net->P,
-                          net->n_pop, net->pop_start, net->ncmax, se, net->d_slots, s));
+    if (e != cudaSuccess) return cuda_fail(e, "segment maxima");
+    std::vector<uint32_t> S(P);
+    std::vector<unsigned long long> base(P);
+    uint64_t total = 0;
+    int smax = 32;
+    for (int c = 0; c < P; ++c) {
+        uint32_t se = 32;
+        while (se < lmax[c] + 1) se *= 2;
+        S[c] = se;
+        base[c] = total;
+        total += (uint64_t)net->n * se;
+        smax = std::max(smax, (int)se);
+    }
+    net->slot_entries = smax;
+    net->slot_total = total;
+    CALL(dalloc(&net->d_slot_base, P, "slot offsets"));
+    CALL(dalloc(&net->d_slot_S, P, "slot strides"));
+    CK(cudaMemcpyAsync(net->d_slot_base, base.data(), sizeof(unsigned long long) * P,
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(net->d_slot_S, S.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, s));
+    CALL(dalloc(&net->d_slots, (size_t)total + 32, "partition slots"));
+    CK(launch_build_slots(net->d_words, net->d_seg, net->d_part_lo, net->d_wtab, net->n, P,
+                          net->n_pop, net->pop_start, net->ncmax, net->d_slot_base, net->d_slot_S,
+                          net->d_slots, s));
     CK(cudaStreamSynchronize(s));
     return SNN_OK;
 }
@@ -527,7 +548,8 @@ void fill_step_params(const snn_net* net, StepParams* out) {
         for (int m = 0; m < kPoisTable; ++m)   // T >= 1 (validation bounds lambda)
             sp.pois_m1[p][m] = (uint32_t)(net->pois[p][m] - 1u);
     sp.slots = net->d_slots;
-    sp.slot_entries = net->slot_entries;
+    sp.slot_base = net->d_slot_base;
+    sp.slot_S = net->d_slot_S;
     sp.part_lo = net->d_part_lo;
     sp.seg = net->d_seg;
     sp.words = net->d_words;
@@ -585,7 +607,8 @@ int net_upload_weights(snn_net* net) {
     cudaStream_t s = net->stream;
     CK(cudaMemcpyAsync(net->d_wtab, net->wtab, sizeof(net->wtab), cudaMemcpyHostToDevice, s));
     CK(launch_build_slots(net->d_words, net->d_seg, net->d_part_lo, net->d_wtab, net->n, net->P,
-                          net->n_pop, net->pop_start, net->ncmax, net->slot_entries, net->d_slots,
+                          net->n_pop, net->pop_start, net->ncmax, net->d_slot_base, net->d_slot_S,
+                          net->d_slots,
                           s));
     CK(cudaStreamSynchronize(s));
     return SNN_OK;
@@ -658,7 +681,7 @@ int snn_read_spikes(snn_net* net, uint32_t* steps_host, uint32_t* ids_host, int6
     std::vector<uint32_t> cnt(net->P);
     CK(cudaMemcpy(cnt.data(), net->d_ras_n, sizeof(uint32_t) * net->P, cudaMemcpyDeviceToHost));
     int64_t got = 0;
-    bool lost = false;
+    bool lost = false, short_cap = false;
     for (int c = 0; c < net->P; ++c) {
         uint32_t m = cnt[c];
         if (m > net->ras_cap) {
@@ -666,7 +689,7 @@ int snn_read_spikes(snn_net* net, uint32_t* steps_host, uint32_t* ids_host, int6
             m = net->ras_cap;
         }
         const int64_t take = std::min<int64_t>(m, cap - got);
-        if (take < (int64_t)m) lost = true;
+        if (take < (int64_t)m) short_cap = true;
         if (take > 0) {
             if (steps_host)
                 CK(cudaMemcpy(steps_host + got, net->d_ras_step + (size_t)c * net->ras_cap,
@@ -681,6 +704,7 @@ int snn_read_spikes(snn_net* net, uint32_t* steps_host, uint32_t* ids_host, int6
     CK(cudaStreamSynchronize(net->stream));
     *n = got;
     if (lost) return fail(SNN_ERR_OVERFLOW, "spike raster capacity exceeded; spikes were lost");
+    if (short_cap) return fail(SNN_ERR_OVERFLOW, "cap smaller than the recorded spikes; the rest were dropped");
     return SNN_OK;
 }
 

@@ -45,8 +45,11 @@ struct snn_net {
     float* d_i = nullptr;
     int32_t* d_r = nullptr;
     int32_t* d_ring = nullptr;
-    int2* d_slots = nullptr;               // [P][n][slot_entries] (weight, ring offset)
-    int32_t slot_entries = 0;
+    int2* d_slots = nullptr;               // partition c: [n][S_c] (weight, ring offset)
+    unsigned long long* d_slot_base = nullptr;  // [P] first entry of partition c
+    uint32_t* d_slot_S = nullptr;          // [P] S_c = entries per slot of partition c
+    int32_t slot_entries = 0;              // largest S_c
+    uint64_t slot_total = 0;               // entries allocated
     unsigned long long* d_msg = nullptr;   // [4][P][msg_stride] tagged spike messages
     int32_t msg_stride = 0;
     uint32_t* d_ras_step = nullptr;

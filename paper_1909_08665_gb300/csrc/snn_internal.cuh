@@ -150,7 +150,7 @@ struct StepParams {
     uint64_t timeout_ns;
     int32_t inject_fault;               // 1: partition 0 never publishes
     int32_t msg_stride;                 // 64-bit words per message (>= ncmax + 1)
-    int32_t slot_entries;               // 8-byte entries per partition slot (power of 2, >= 32)
+    int32_t pad_slots;
     uint32_t pois_m1[kMaxPop][kPoisTable];  // Poisson thresholds minus 1 (x > T-1 -> +1)
     // network (read only)
     const int32_t* part_lo;             // [n_part + 1]
@@ -158,7 +158,9 @@ struct StepParams {
     const uint32_t* words;
     const int32_t* wtab;                // [8][8][128]
     const unsigned long long* row_start;  // [n + 1] row offsets
-    const int2* slots;                  // [n_part][n][slot_entries] (weight, ring offset)
+    const int2* slots;                  // partition c: [n][slot_S[c]] (weight, ring offset) at slot_base[c]
+    const unsigned long long* slot_base;  // [n_part] first entry of each partition's slots
+    const uint32_t* slot_S;             // [n_part] entries per slot (power of 2, >= 32)
     // state
     float* u;
     float* i_syn;
@@ -211,12 +213,14 @@ cudaError_t launch_build_fill(const BuildParams& bp, const unsigned long long* r
 cudaError_t launch_seg_from_rows(const unsigned long long* row_start, const uint32_t* words,
                                  int n, const int32_t* part_lo, int n_part, uint32_t* seg,
                                  cudaStream_t s);
+// out[c] = longest (row, partition c) segment, for every partition c
 cudaError_t launch_max_segment(const uint32_t* seg, int n, int n_part, uint32_t* out,
                                cudaStream_t s);
 cudaError_t launch_build_slots(const uint32_t* words, const uint32_t* seg, const int32_t* part_lo,
                                const int32_t* wtab, int n, int n_part, int n_pop,
-                               const int32_t* pop_start, int ncmax, int slot_entries, int2* slots,
-                               cudaStream_t s);
+                               const int32_t* pop_start, int ncmax,
+                               const unsigned long long* slot_base, const uint32_t* slot_S,
+                               int2* slots, cudaStream_t s);
 cudaError_t launch_init_state(int n, uint32_t key0, uint32_t key1, float lo, float hi,
                               float* u, cudaStream_t s);
 int step_kernel_variant(int npt, bool smem_ring);

@@ -39,7 +39,8 @@ namespace snn {
 
 constexpr int kWarps = kStepThreads / 32;
 constexpr uint32_t kStatusRasterOverflow = 2u;
-constexpr int kInline = 7;        // ids read together with a message header (64 B)
+constexpr int kInline = 7;
+constexpr int kSlotWave = 4;            // slot entries per lane loaded at once (128 per slot)        // ids read together with a message header (64 B)
 
 // ---------------------------------------------------------------------------
 // shared-memory layout (bytes), identical on host and device
@@ -138,36 +139,40 @@ __device__ __forceinline__ void deliver_batches(const StepParams& sp, const uint
                                                 uint32_t m, int c, int64_t tb, int32_t* ring,
                                                 unsigned long long& events) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t S_e = (uint32_t)sp.slot_entries;
+    // this partition's slots: stride S_c entries, the first min(S_c, 128)
+    // of each slot loaded in one wave (NE entries per lane)
+    const uint32_t S_c = __ldg(&sp.slot_S[c]);
+    const int2* sbase = sp.slots + __ldg(&sp.slot_base[c]);
+    const uint32_t NE = min(S_c >> 5, (uint32_t)kSlotWave);
     const int32_t R = kRing * sp.ncmax;                  // ring words of this CTA
     const int32_t base_t = (int32_t)(((uint32_t)tb & (kRing - 1)) * (uint32_t)sp.ncmax);
-    const size_t part_base = (size_t)c * (size_t)sp.n;
     for (uint32_t g0 = (uint32_t)warp * 4u; g0 < m; g0 += (uint32_t)kWarps * 4u) {
         const int2* sl[4];
-        int2 ev[4][2];
+        int2 ev[4][kSlotWave];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const bool ok = g0 + (uint32_t)k < m;
             const uint32_t id = ok ? s_spk[g0 + k] : 0u;
-            sl[k] = sp.slots + (part_base + id) * S_e;
-            ev[k][0] = ok ? __ldg(sl[k] + lane) : make_int2(0, 0);
-            ev[k][1] = (ok && S_e > 32u) ? __ldg(sl[k] + 32 + lane) : make_int2(0, 0);
+            sl[k] = sbase + (size_t)id * S_c;
+#pragma unroll
+            for (int h = 0; h < kSlotWave; ++h)
+                ev[k][h] = (ok && (uint32_t)h < NE) ? __ldg(sl[k] + 32 * h + lane) : make_int2(0, 0);
         }
         // entry 0 of a slot is its count; entry e >= 1 is (weight, offset)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const uint32_t cnt = (uint32_t)__shfl_sync(0xffffffffu, ev[k][0].x, 0);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kSlotWave; ++h) {
                 const uint32_t e = (uint32_t)lane + 32u * (uint32_t)h;
-                if (e >= 1u && e <= cnt) {
+                if ((uint32_t)h < NE && e >= 1u && e <= cnt) {
                     int32_t a = base_t + ev[k][h].y;
                     a -= a >= R ? R : 0;
                     atomicAdd(&ring[a], ev[k][h].x);
                 }
             }
-            // slots longer than 63 entries (few partitions only)
-            for (uint32_t e = 64u + (uint32_t)lane; e <= cnt; e += 32u) {
+            // entries beyond the first wave (partitions with S_c > 32 kSlotWave)
+            for (uint32_t e = 32u * NE + (uint32_t)lane; e <= cnt; e += 32u) {
                 const int2 x = __ldg(sl[k] + e);
                 int32_t a = base_t + x.y;
                 a -= a >= R ? R : 0;
