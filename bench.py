@@ -27,6 +27,8 @@ Other workloads (--workload; the default line is the full microcircuit):
           biological of every instance; synaptic events/s over all instances
   grad    one surrogate-gradient evaluation (forward with checkpoints every
           100 steps + backward) of the 10 % microcircuit over 200 ms
+  deliver the delivery kernels alone on spike lists of 25 / 93 / 4,000 /
+          20,000 random sources at scales 1 and 4 (HBM roofline per case)
 """
 import argparse
 import json
@@ -45,6 +47,10 @@ METRIC = "real-time factor and synaptic events/s (full microcircuit, 1 GB300); %
 UNIT = "synaptic events/s"
 STEPS_PER_BENCH_STEP = 10000          # 1 s of biological time at dt = 0.1 ms
 BYTES_PER_EVENT = 4                   # one packed synaptic word read per event
+# DRAM bytes (read + write) per time step of k_step on the full microcircuit,
+# from one ncu capture of this kernel (profiles/k_step_full_microcircuit_dram.md);
+# None for any other workload, and to be re-measured whenever k_step changes
+K_STEP_DRAM_BYTES_PER_STEP_FULL = (14163306240 + 4550400) / 2000.0
 
 
 def load_peaks():
@@ -284,6 +290,7 @@ def run_ours(args):
                    "l2": "no flush: synapse rows (%.2f GB) exceed the 129 MB L2"
                          % (info["n_synapses"] * 4 / 1e9),
                    "n_part": info["n_part"], "ring_in_shared": info["ring_in_shared"],
+                   "slot_gb": info["slot_bytes"] / 1e9,
                    "parallelism": "replicas" if ws > 1 else "single"},
         "spikes_per_time_step": spikes / (args.steps * chunk),
         "events_per_time_step": events / (args.steps * chunk),
@@ -295,7 +302,13 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h // max(args.steps, 1),
                 "real_time_factor": e2e_s / bio_s},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak,
+                     "traffic": (K_STEP_DRAM_BYTES_PER_STEP_FULL * chunk
+                                 if args.scale == 1.0 else None),
+                     "traffic_source": ("ncu dram__bytes of one 2000-step launch, scaled by "
+                                        "steps per launch (profiles/"
+                                        "k_step_full_microcircuit_dram.md)"
+                                        if args.scale == 1.0 else None),
                      "peak_kind": peak_kind, "kernel": "k_step (persistent step kernel)"},
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.scale <= 1.0:
@@ -401,6 +414,69 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def run_deliver(args):
+    """Delivery microbenchmark (a5 alone): one spike list of m random sources
+    through snn_deliver, for m = 25 (mean activity), 93 (peak), 4,000 (the
+    initial transient) and 20,000, at scale 1 and 4.  Each repetition draws a
+    fresh list from a pool whose rows together exceed L2 several times."""
+    import torch
+
+    import paper_1909_08665_gb300 as pkg
+    import workload
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    hbm_peak, peak_kind = load_peaks()
+    rows = []
+    rng = np.random.default_rng(99)
+    for scale in (1.0, 4.0):
+        net = pkg.Microcircuit(workload.microcircuit(scale), stream=stream)
+        rp, _, _ = net.export_network(rows_only=True)
+        row_len = np.diff(rp.astype(np.int64))
+        for m in (25, 93, 4000, 20000):
+            for tiling in (0, 1, 2):
+                # pool of lists: at least 1 GB of rows in total, 8 lists minimum
+                per_list = float(row_len.mean()) * 4 * m
+                n_lists = int(min(256, max(8, np.ceil(1.0e9 / per_list))))
+                lists = [np.sort(rng.choice(net.n, m, replace=False)).astype(np.int32)
+                         for _ in range(n_lists)]
+                dev = [torch.from_numpy(x).cuda() for x in lists]
+                events = [int(row_len[x].sum()) for x in lists]
+                for k in range(min(3, n_lists)):                 # warm-up
+                    net.deliver(dev[k].data_ptr(), m, k, tiling)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                reps = n_lists
+                e0.record(stream)
+                for k in range(reps):
+                    net.deliver(dev[k].data_ptr(), m, 7 + k, tiling)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                ev = float(np.mean(events[:reps]))
+                gbs = 4.0 * ev / (ms * 1e-3) / 1e9
+                rows.append({"scale": scale, "spikes": m,
+                             "tiling": ["warp", "block", "partition"][tiling],
+                             "us": ms * 1e3, "events": ev, "achieved_gbs": gbs,
+                             "frac": gbs / hbm_peak})
+        net.close()
+    best = max(rows, key=lambda r: r["achieved_gbs"])
+    line = {
+        "metric": "synaptic events/s of the delivery kernels alone (one spike list per launch)",
+        "value": best["events"] / (best["us"] * 1e-6), "unit": "synaptic events/s", "n_gpus": 1,
+        "steps": None, "warmup": 3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {"workload": "snn_deliver of random spike lists at scales 1 and 4; lists drawn "
+                               "from pools of >= 1 GB of rows (no list repeats within a timing)"},
+        "roofline": {"bound": "hbm", "achieved": best["achieved_gbs"], "peak": hbm_peak,
+                     "unit": "GB/s", "frac": best["frac"], "traffic": None,
+                     "peak_kind": peak_kind, "kernel": "k_deliver_%s" % best["tiling"]},
+        "cases": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_grad(args):
     import torch
 
@@ -467,7 +543,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4000)
     ap.add_argument("--ref-chunk", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="full", choices=["full", "scale4", "batch", "grad"])
+    ap.add_argument("--workload", default="full",
+                    choices=["full", "scale4", "batch", "grad", "deliver"])
     args = ap.parse_args()
     if args.workload == "scale4":
         args.scale = 4.0
@@ -477,6 +554,8 @@ def main():
         run_batch(args)
     elif args.workload == "grad":
         run_grad(args)
+    elif args.workload == "deliver":
+        run_deliver(args)
     else:
         run_ours(args)
 

@@ -106,7 +106,8 @@ typedef struct snn_info {
     float propagators[4];     /* P22, P21, P11, P20 as used (fp32) */
     int32_t wext_q;           /* background weight, 1/256 pA */
     int32_t shared_bytes;     /* dynamic shared memory of the step kernel */
-    int32_t slot_entries;     /* 8-byte entries per (row, partition) slot */
+    int32_t slot_entries;     /* largest per-partition slot stride S_c (8-byte entries) */
+    int64_t slot_bytes;       /* device memory of the partition slots */
 } snn_info;
 
 typedef struct snn_net snn_net;
@@ -194,7 +195,9 @@ int snn_export_network(snn_net* net, uint64_t* row_ptr_host, uint32_t* words_hos
  * snn_deliver -- deliver one arbitrary spike list into the ring buffers, as
  * step 6 does for the spikes of step t (Sec. 3.1.2: row fetch, word decode,
  * buffer add).  spikes_dev: device array of n_spikes neuron ids (duplicates
- * allowed).  tiling 0: one warp per spike; 1: one CTA per spike row.
+ * allowed).  tiling 0: one warp per spike; 1: one CTA per spike row; 2: one
+ * CTA per partition, through the partition slots as in snn_step (the ring
+ * slice in shared memory when it fits).
  * Asynchronous on the network's stream; adds to the existing ring content.
  */
 int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int64_t t,
@@ -318,7 +321,12 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
  * 5 Hz x N x 0.1 ms), one warp per spike (tiling 0), one CTA per row
  * (tiling 1) and flat (tiling 2: the rows of all flat-tiled spikes of a step
  * concatenated and spread over every warp of the grid), and keeps the
- * fastest; snn_batch_get_info reports the three times.
+ * fastest.  Because all instances' spikes share the grid in the batch, it
+ * then times the persistent kernel itself (100 + 300 steps) under candidate
+ * assignments -- the probes' choices, each tiling for every instance, and the
+ * smaller and larger half of the instances on two different tilings -- keeps
+ * the fastest, and resets every instance to its initial state.
+ * snn_batch_get_info reports the probe times and the chosen per-step time.
  *
  * Steps are issued as replays of one captured CUDA graph of 1000 steps; the
  * kernel reads its first step index from device memory and advances it, so
@@ -337,6 +345,8 @@ typedef struct snn_batch_info {
     float tune_us_warp;          /* autotuner probe times, microseconds */
     float tune_us_block;
     float tune_us_flat;
+    float trial_us_per_step;     /* the chosen assignment's time per step in the
+                                    autotuner's batch trials */
     int32_t blocks, threads, neurons_per_thread;
     int32_t graph;               /* 1 if the graph was captured */
     int32_t graph_steps;         /* steps per graph replay */

@@ -74,7 +74,8 @@ class SnnInfo(C.Structure):
                 ("threads", C.c_int32), ("neurons_per_thread", C.c_int32),
                 ("ring_in_shared", C.c_int32), ("max_part_neurons", C.c_int32),
                 ("n_ref", C.c_int32), ("propagators", C.c_float * 4), ("wext_q", C.c_int32),
-                ("shared_bytes", C.c_int32), ("slot_entries", C.c_int32)]
+                ("shared_bytes", C.c_int32), ("slot_entries", C.c_int32),
+                ("slot_bytes", C.c_int64)]
 
 
 class SnnNoallocIO(C.Structure):
@@ -90,7 +91,7 @@ class SnnBatchInfo(C.Structure):
     _fields_ = [("n_instances", C.c_int32), ("n_neurons_total", C.c_int32),
                 ("n_neurons", C.c_int32), ("n_synapses", C.c_int64), ("tiling", C.c_int32),
                 ("tune_us_warp", C.c_float), ("tune_us_block", C.c_float),
-                ("tune_us_flat", C.c_float),
+                ("tune_us_flat", C.c_float), ("trial_us_per_step", C.c_float),
                 ("blocks", C.c_int32), ("threads", C.c_int32),
                 ("neurons_per_thread", C.c_int32), ("graph", C.c_int32),
                 ("graph_steps", C.c_int32)]
@@ -341,14 +342,16 @@ class Microcircuit:
                                        C.byref(gn)))
         return ga.reshape(MAX_POP, MAX_POP), gn.value
 
-    def export_network(self):
+    def export_network(self, rows_only: bool = False):
+        """(row_ptr, words, wtab); words is None with rows_only."""
         inf = self.info()
         rp = np.zeros(self.n + 1, np.uint64)
-        wd = np.zeros(max(int(inf["n_synapses"]), 1), np.uint32)
+        wd = None if rows_only else np.zeros(max(int(inf["n_synapses"]), 1), np.uint32)
         wt = np.zeros(MAX_POP * MAX_POP * WCODES, np.int32)
         _check(lib().snn_export_network(self._h, _ptr(rp, C.c_uint64), _ptr(wd, C.c_uint32),
                                         _ptr(wt, C.c_int32)))
-        return rp, wd[:int(inf["n_synapses"])], wt.reshape(MAX_POP, MAX_POP, WCODES)
+        words = None if rows_only else wd[:int(inf["n_synapses"])]
+        return rp, words, wt.reshape(MAX_POP, MAX_POP, WCODES)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -570,6 +570,8 @@ struct snn_batch {
     bool graph_ok = false;
     long long step = 0;
     std::vector<std::vector<uint32_t>> host_steps, host_ids;   // drained raster per instance
+    std::vector<float2> u0_range;        // default initial potentials per instance
+    float trial_us = 0.f;                // per-step time of the chosen assignment
 };
 
 namespace {
@@ -686,6 +688,89 @@ int autotune(snn_batch* b) {
     return SNN_OK;
 }
 
+// every instance back to its initial state (after the autotuner's trials)
+cudaError_t reset_state(snn_batch* b) {
+    cudaStream_t s = b->stream;
+    const size_t ntot = (size_t)b->ntot;
+    cudaError_t e = cudaMemsetAsync(b->d_i, 0, sizeof(float) * ntot, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_r, 0, sizeof(int32_t) * ntot, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ring, 0, sizeof(int32_t) * (size_t)kRing * ntot, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cnt, 0, sizeof(uint32_t) * 4 * kTilings, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ras_n, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ic, 0, sizeof(unsigned long long) * 2 * b->n_inst, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_step, 0, sizeof(long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync, 0, sizeof(uint32_t) * 4, s);
+    for (int k = 0; k < b->n_inst && e == cudaSuccess; ++k) {
+        const InstHot& H = b->hot_h[k];
+        e = launch_init_state((int)H.key.w, H.key.x, H.key.y, b->u0_range[k].x, b->u0_range[k].y,
+                              b->d_u + H.misc.w, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
+// Batch-level trials: the persistent kernel itself, 100 + 300 steps, under
+// candidate tiling assignments (the per-instance probe choice, each tiling for
+// every instance, and the smaller / larger half of the instances on two
+// different tilings); the fastest is kept.  The probes time each instance
+// alone, while in the batch all instances' spikes share the grid, so the
+// trials decide.  The state is reset to the initial state afterwards.
+int batch_trials(snn_batch* b) {
+    cudaStream_t s = b->stream;
+    const int K = b->n_inst;
+    std::vector<std::vector<uint32_t>> cand;
+    std::vector<uint32_t> probe(K);
+    for (int k = 0; k < K; ++k) probe[k] = b->hot_h[k].key.z;
+    cand.push_back(probe);
+    for (uint32_t tl = 0; tl < (uint32_t)kTilings; ++tl) cand.push_back(std::vector<uint32_t>(K, tl));
+    if (K > 1) {
+        std::vector<int> order(K);
+        for (int k = 0; k < K; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int c) { return b->cold_h[a].n < b->cold_h[c].n; });
+        for (uint32_t x = 0; x < (uint32_t)kTilings; ++x)
+            for (uint32_t y = 0; y < (uint32_t)kTilings; ++y) {
+                if (x == y) continue;
+                std::vector<uint32_t> a(K);
+                for (int r = 0; r < K; ++r) a[order[r]] = r < K / 2 ? x : y;
+                cand.push_back(a);
+            }
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    size_t best_c = 0;
+    cudaError_t e = cudaSuccess;
+    for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
+        for (int k = 0; k < K; ++k) b->hot_h[k].key.z = cand[c][k];
+        e = cudaMemcpyAsync(b->d_hot, b->hot_h.data(), sizeof(InstHot) * K, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = reset_state(b);
+        if (e == cudaSuccess) e = launch_batch(b, 100);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = launch_batch(b, 300);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return set_cuda_error(e, "batch autotune trials");
+    uint32_t st = 0;
+    BCK(cudaMemcpy(&st, b->d_sync + 1, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st & kStatusTimeout) return set_error(SNN_ERR_TIMEOUT, "a grid-barrier wait timed out");
+    for (int k = 0; k < K; ++k) b->hot_h[k].key.z = cand[best_c][k];
+    b->trial_us = best * 1000.f / 300.f;
+    BCK(cudaMemcpyAsync(b->d_hot, b->hot_h.data(), sizeof(InstHot) * K, cudaMemcpyHostToDevice, s));
+    BCK(reset_state(b));
+    return SNN_OK;
+}
+
 int drain_raster(snn_batch* b) {
     BCK(cudaStreamSynchronize(b->stream));
     uint32_t n = 0;
@@ -772,6 +857,7 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
             ps_all[(size_t)k * 8 + m] = m == 0 ? 0 : (m < ht.n_pop ? ht.pop_start[m] : 0x7fffffff);
         C.row_start = rs;
         C.words = wd;
+        b->u0_range.push_back(make_float2((float)cfgs[k].u0_lo, (float)cfgs[k].u0_hi));
         ntot += ht.n;
         b->goff[k + 1] = (int32_t)ntot;
         if (ntot > (1ll << 30)) rc = set_error(SNN_ERR_INVALID, "too many neurons in the batch");
@@ -901,6 +987,7 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
         return set_error(SNN_ERR_CUDA, "probe kernel shared memory");
     }
     rc = autotune(b);
+    if (rc == SNN_OK && !(opt && opt->inject_fault)) rc = batch_trials(b);
     if (rc != SNN_OK) {
         free_batch(b);
         return rc;
@@ -1013,6 +1100,7 @@ int snn_batch_get_info(snn_batch* b, int32_t k, snn_batch_info* info) {
     info->tune_us_warp = b->tune_us[0][k];
     info->tune_us_block = b->tune_us[1][k];
     info->tune_us_flat = b->tune_us[2][k];
+    info->trial_us_per_step = b->trial_us;
     info->blocks = b->blocks;
     info->threads = kBThreads;
     info->neurons_per_thread = b->npt;

@@ -608,8 +608,7 @@ int net_upload_weights(snn_net* net) {
     CK(cudaMemcpyAsync(net->d_wtab, net->wtab, sizeof(net->wtab), cudaMemcpyHostToDevice, s));
     CK(launch_build_slots(net->d_words, net->d_seg, net->d_part_lo, net->d_wtab, net->n, net->P,
                           net->n_pop, net->pop_start, net->ncmax, net->d_slot_base, net->d_slot_S,
-                          net->d_slots,
-                          s));
+                          net->d_slots, s));
     CK(cudaStreamSynchronize(s));
     return SNN_OK;
 }
@@ -768,6 +767,7 @@ int snn_get_info(snn_net* net, snn_info* info) {
     info->wext_q = net->wext_q;
     info->shared_bytes = (int32_t)net->smem;
     info->slot_entries = net->slot_entries;
+    info->slot_bytes = (int64_t)(net->slot_total * sizeof(int2));
     return SNN_OK;
 }
 
@@ -786,8 +786,14 @@ int snn_export_network(snn_net* net, uint64_t* row_ptr_host, uint32_t* words_hos
 
 int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int64_t t,
                 int32_t tiling) {
-    if (!net || n_spikes < 0 || (n_spikes > 0 && !spikes_dev) || (tiling != 0 && tiling != 1))
+    if (!net || n_spikes < 0 || (n_spikes > 0 && !spikes_dev) || tiling < 0 || tiling > 2)
         return fail(SNN_ERR_INVALID, "bad arguments");
+    if (tiling == 2) {
+        StepParams sp;
+        fill_step_params(net, &sp);
+        CK(launch_deliver_part(sp, spikes_dev, n_spikes, t, net->smem_ring, net->stream));
+        return SNN_OK;
+    }
     DeliverParams dp;
     std::memset(&dp, 0, sizeof(dp));
     dp.n = net->n;

@@ -64,6 +64,9 @@ struct snn_grad {
     uint32_t* saved_ras = nullptr;  // raster counts
     uint32_t* saved_status = nullptr;
     int32_t* pop_start = nullptr;   // [9]
+    int32_t* blk = nullptr;         // [grid + 1] row range of each adjoint CTA
+    int32_t* order = nullptr;       // [n] each CTA's rows, longest first
+    int32_t grid = 0, chunk = 0;    // CTAs of the adjoint, most rows of one CTA
 };
 
 namespace snn {
@@ -72,7 +75,7 @@ void free_grad(snn_grad* g) {
     if (!g) return;
     void* ptrs[] = {g->ckpt, g->tr_u, g->tr_f, g->lu, g->lI, g->lring, g->mnext, g->gA, g->gN,
                     g->wbase, g->out, g->sync, g->saved, g->saved_ras, g->saved_status,
-                    g->pop_start};
+                    g->pop_start, g->blk, g->order};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -90,6 +93,8 @@ constexpr int kAdjUnroll = 8;           // row words per lane in flight
 
 struct AdjParams {
     int32_t n, n_pop, len, chunk;
+    const int32_t* blk;              // [grid + 1] row range of each CTA
+    const int32_t* order;            // [n] rows of each CTA, longest first
     int32_t pop_start[kMaxPop + 1];
     int64_t t_first;                 // global step of trace row 0
     float P22, P21, P11, theta;
@@ -124,10 +129,11 @@ __device__ __forceinline__ float surrogate_slope(float x) {
     return __fdiv_rn(1.0f, __fmul_rn(a, a));
 }
 
-// The adjoint of trace rows len-1 .. 0.  CTA b owns neurons
-// [b chunk, (b + 1) chunk): their rows in the spike phase and their state in
-// the membrane phase; one grid barrier per step separates the lI writes of
-// step t from the row gathers of step t - 1.
+// The adjoint of trace rows len-1 .. 0.  CTA b owns neurons [blk[b],
+// blk[b + 1]) (ranges balanced by total row length): their rows in the spike
+// phase, taken by the warps longest first, and their state in the membrane
+// phase; one grid barrier per step separates the lI writes of step t from the
+// row gathers of step t - 1.
 __global__ void __launch_bounds__(kAdjThreads, 1) k_adjoint(const __grid_constant__ AdjParams p) {
     // dynamic shared memory: row starts of the CTA's rows [chunk + 1] (u64),
     // then the spike adjoints of the current step [chunk]
@@ -135,8 +141,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adjoint(const __grid_constan
     float* s_ds = reinterpret_cast<float*>(s_rs + p.chunk + 1);
     __shared__ volatile uint32_t s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int32_t lo = min(p.n, (int32_t)blockIdx.x * p.chunk);
-    const int32_t hi = min(p.n, lo + p.chunk);
+    const int32_t lo = p.blk[blockIdx.x];
+    const int32_t hi = p.blk[blockIdx.x + 1];
     if (tid == 0) s_abort = 0u;
     for (int32_t j = lo + tid; j <= hi; j += kAdjThreads) s_rs[j - lo] = p.row_start[j];
     __syncthreads();
@@ -146,7 +152,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adjoint(const __grid_constan
         const int64_t t = p.t_first + s;
         const uint8_t* fl = p.tr_f + (size_t)s * n;
         // ---- spike adjoints: loss term plus the rows' pull from lI(t + d) ----
-        for (int32_t j = lo + warp; j < hi; j += kAdjWarps) {
+        for (int32_t r = lo + warp; r < hi; r += kAdjWarps) {
+            const int32_t j = __ldg(&p.order[r]);
             const int q = pop_index(p.pop_start, p.n_pop, j);
             const bool spk = (fl[j] & 1u) != 0u;
             int32_t ps[kMaxPop];
@@ -464,15 +471,43 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
     GCK(cudaMemcpyAsync(g->out + kMaxPop * kMaxPop + 1, dnu, sizeof(dnu), cudaMemcpyHostToDevice, s));
     GCK(cudaMemcpyAsync(g->pop_start, net->pop_start, sizeof(int32_t) * (kMaxPop + 1), cudaMemcpyHostToDevice, s));
 
-    int dev = 0, sms = 0;
-    GCK(cudaGetDevice(&dev));
-    GCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int grid = std::max(1, std::min(sms, (n + 31) / 32));
+    if (!g->blk) {
+        // CTA row ranges with equal total row length, rows longest first
+        int dev = 0, sms = 0;
+        GCK(cudaGetDevice(&dev));
+        GCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int grid = std::max(1, std::min(sms, (n + 31) / 32));
+        std::vector<unsigned long long> rs(n + 1);
+        GCK(cudaMemcpy(rs.data(), net->d_row_start, sizeof(unsigned long long) * (n + 1),
+                       cudaMemcpyDeviceToHost));
+        std::vector<int32_t> blk(grid + 1, n), order(n);
+        blk[0] = 0;
+        const double total = (double)rs[n] + (double)n;     // + 1 per row: empty rows cost too
+        int b = 1;
+        for (int j = 0; j < n && b < grid; ++j)
+            while (b < grid && (double)rs[j + 1] + (double)(j + 1) >= total * b / grid) blk[b++] = j + 1;
+        int chunk = 1;
+        for (int c = 0; c < grid; ++c) {
+            for (int j = blk[c]; j < blk[c + 1]; ++j) order[j] = j;
+            std::stable_sort(order.begin() + blk[c], order.begin() + blk[c + 1],
+                             [&](int x, int y) { return rs[x + 1] - rs[x] > rs[y + 1] - rs[y]; });
+            chunk = std::max(chunk, blk[c + 1] - blk[c]);
+        }
+        GCALL(galloc(&g->blk, grid + 1, "adjoint ranges"));
+        GCALL(galloc(&g->order, n, "adjoint row order"));
+        GCK(cudaMemcpy(g->blk, blk.data(), sizeof(int32_t) * (grid + 1), cudaMemcpyHostToDevice));
+        GCK(cudaMemcpy(g->order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+        g->grid = grid;
+        g->chunk = chunk;
+    }
+    const int grid = g->grid;
     AdjParams ap;
     std::memset(&ap, 0, sizeof(ap));
     ap.n = n;
     ap.n_pop = net->n_pop;
-    ap.chunk = (n + grid - 1) / grid;
+    ap.chunk = g->chunk;
+    ap.blk = g->blk;
+    ap.order = g->order;
     for (int p = 0; p <= kMaxPop; ++p) ap.pop_start[p] = net->pop_start[p];
     ap.P22 = net->prop[0];
     ap.P21 = net->prop[1];

@@ -229,5 +229,8 @@ cudaError_t step_kernel_configure(int npt, bool smem_ring, size_t smem);
 cudaError_t launch_step(const StepParams& sp, int npt, bool smem_ring, size_t smem,
                         cudaStream_t s);
 cudaError_t launch_deliver(const DeliverParams& dp, int tiling, cudaStream_t s);
+// stand-alone delivery through the partition slots (one CTA per partition)
+cudaError_t launch_deliver_part(const StepParams& sp, const uint32_t* spikes, int n, int64_t t,
+                                bool smem_ring, cudaStream_t s);
 
 }  // namespace snn

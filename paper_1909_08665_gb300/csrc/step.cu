@@ -581,6 +581,50 @@ cudaError_t launch_step(const StepParams& sp, int npt, bool smem_ring, size_t sm
     return cudaLaunchCooperativeKernel(fn, dim3(sp.n_part), dim3(kStepThreads), args, smem, s);
 }
 
+// Partition tiling of the stand-alone delivery: CTA c takes every spike of
+// the list through its partition slots (the step kernel's delivery), with its
+// ring slice staged in shared memory when it fits.
+template <bool SMEM_RING>
+__global__ void __launch_bounds__(kStepThreads, 1)
+k_deliver_part(const __grid_constant__ StepParams sp, const uint32_t* __restrict__ spikes, int n,
+               int64_t t) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* s_spk = reinterpret_cast<uint32_t*>(smem);
+    const int c = blockIdx.x, tid = threadIdx.x;
+    const int R = kRing * sp.ncmax;
+    int32_t* ring_g = sp.ring + (size_t)c * R;
+    int32_t* ring = SMEM_RING ? reinterpret_cast<int32_t*>(s_spk + kChunk) : ring_g;
+    if (SMEM_RING)
+        for (int k = tid; k < R; k += kStepThreads) ring[k] = ring_g[k];
+    __syncthreads();
+    unsigned long long events = 0;
+    for (int base = 0; base < n; base += kChunk) {
+        const int m = min(kChunk, n - base);
+        for (int k = tid; k < m; k += kStepThreads) s_spk[k] = __ldg(&spikes[base + k]);
+        __syncthreads();
+        deliver_batches(sp, s_spk, (uint32_t)m, c, t, ring, events);
+        __syncthreads();
+    }
+    if (SMEM_RING)
+        for (int k = tid; k < R; k += kStepThreads) ring_g[k] = ring[k];
+    if ((tid & 31) == 0 && events) atomicAdd(&sp.counters[1], events);
+}
+
+cudaError_t launch_deliver_part(const StepParams& sp, const uint32_t* spikes, int n, int64_t t,
+                                bool smem_ring, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = (size_t)kChunk * 4 + (smem_ring ? (size_t)kRing * sp.ncmax * 4 : 0);
+    const void* fn = smem_ring ? reinterpret_cast<const void*>(&k_deliver_part<true>)
+                               : reinterpret_cast<const void*>(&k_deliver_part<false>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (smem_ring)
+        k_deliver_part<true><<<sp.n_part, kStepThreads, smem, s>>>(sp, spikes, n, t);
+    else
+        k_deliver_part<false><<<sp.n_part, kStepThreads, smem, s>>>(sp, spikes, n, t);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_deliver(const DeliverParams& dp, int tiling, cudaStream_t s) {
     if (dp.n_spikes <= 0) return cudaSuccess;
     if (tiling == 0) {

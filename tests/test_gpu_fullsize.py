@@ -68,7 +68,7 @@ def test_full_size_raster_bit_exact_100_steps(full):
 def test_full_size_delivery_both_tilings(full):
     cfg, net = full
     onet = oracle.Network(cfg, n_threads=os.cpu_count())
-    for tiling in (0, 1):
+    for tiling in (0, 1, 2):
         fresh = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
         spikes = workload.random_spike_list(fresh.n, 4000, seed=11 + tiling)
         d = torch.from_numpy(spikes.astype(np.int32)).cuda()

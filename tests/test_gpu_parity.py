@@ -194,10 +194,10 @@ def test_empty_network_and_zero_steps():
 
 
 # ---------------------------------------------------------------------------
-# standalone delivery: both tilings against the oracle
+# standalone delivery: every tiling against the oracle
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("n_spikes", [1, 25, 93, 4000])
-@pytest.mark.parametrize("tiling", [0, 1])
+@pytest.mark.parametrize("tiling", [0, 1, 2])
 def test_deliver_matches_oracle(cfg01, onet01, n_spikes, tiling):
     net = gpu_net(cfg01)
     spikes = workload.random_spike_list(net.n, n_spikes, seed=n_spikes)
@@ -208,6 +208,18 @@ def test_deliver_matches_oracle(cfg01, onet01, n_spikes, tiling):
     net.sync()
     ref = onet01.deliver(spikes.astype(np.int32), t)
     np.testing.assert_array_equal(net.ring(), ref.astype(np.int32))
+
+
+def test_deliver_partition_tiling_with_global_ring(cfg01, onet01):
+    """Two partitions of 3,859 neurons: the ring does not fit in shared memory
+    and the partition tiling accumulates into global memory."""
+    net = gpu_net(cfg01, n_part=2)
+    assert net.info()["ring_in_shared"] == 0
+    spikes = workload.random_spike_list(net.n, 500, seed=3)
+    d = torch.from_numpy(spikes.astype(np.int32)).cuda()
+    net.deliver(d.data_ptr(), spikes.size, 77, 2)
+    net.sync()
+    np.testing.assert_array_equal(net.ring(), onet01.deliver(spikes.astype(np.int32), 77).astype(np.int32))
 
 
 # ---------------------------------------------------------------------------
