@@ -50,7 +50,7 @@ BYTES_PER_EVENT = 4                   # one packed synaptic word read per event
 # DRAM bytes (read + write) per time step of k_step on the full microcircuit,
 # from one ncu capture of this kernel (profiles/k_step_full_microcircuit_dram.md);
 # None for any other workload, and to be re-measured whenever k_step changes
-K_STEP_DRAM_BYTES_PER_STEP_FULL = (14163306240 + 4550400) / 2000.0
+K_STEP_DRAM_BYTES_PER_STEP_FULL = (14162123008 + 4550912) / 2000.0
 
 
 def load_peaks():
@@ -60,6 +60,20 @@ def load_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def reduce_over_ranks(total_ms, units, device):
+    """Whole-job figures of N replicas: the slowest rank's time (max) and the
+    units (synaptic events) of all ranks (sum).  One rank: unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), float(units)
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
 
 
 def dist_env():
@@ -222,6 +236,9 @@ def run_ours(args):
 
     # -------- device-timed region: K launches, inputs (1.2 GB rows) > L2 --------
     c0 = net.counters()
+    # device clock at the end of every timed step (the real-time criterion)
+    step_clock = torch.zeros(args.steps * chunk, dtype=torch.int64, device=dev)
+    net.record_step_times(step_clock.data_ptr(), args.steps * chunk)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
@@ -236,21 +253,21 @@ def run_ours(args):
         t_all1.record(stream)
         barrier()
     net.sync()
+    net.record_step_times(None)
     c1 = net.counters()
     total_ms = t_all0.elapsed_time(t_all1)
+    stamps = step_clock.cpu().numpy().reshape(args.steps, chunk)
+    dts = np.diff(stamps, axis=1).reshape(-1) * 1e-3         # us, within each launch
+    step_times = {"mean_us": float(dts.mean()) if dts.size else None,
+                  "p99_us": float(np.percentile(dts, 99)) if dts.size else None,
+                  "max_us": float(dts.max()) if dts.size else None,
+                  "steps_over_100us": int((dts > 100.0).sum()),
+                  "source": "device clock at the end of each step (CTA 0), first step of "
+                            "each launch excluded"}
     per_launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     events = c1["events"] - c0["events"]
     spikes = c1["spikes"] - c0["spikes"]
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        e = torch.tensor([float(events)], device=dev, dtype=torch.float64)
-        dist.all_reduce(e)
-        events_all = float(e.item())
-    else:
-        events_all = float(events)
+    total_ms, events_all = reduce_over_ranks(total_ms, events, dev)
     value = events_all / (total_ms * 1e-3)
     bio_s = args.steps * chunk * cfg["dt"] * 1e-3
     rtf = (total_ms * 1e-3) / bio_s
@@ -295,6 +312,7 @@ def run_ours(args):
         "spikes_per_time_step": spikes / (args.steps * chunk),
         "events_per_time_step": events / (args.steps * chunk),
         "us_per_time_step": total_ms * 1e3 / (args.steps * chunk),
+        "step_time": step_times,
         "build_s": build_s,
         "clocks": clk.summary(),
         "gpu_launches": args.steps,
@@ -335,7 +353,7 @@ def run_batch(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    cfgs = workload.batched_instances(64, seed=7 + rank)
+    cfgs = workload.batched_instances(args.instances, seed=7 + rank)
     t_build = time.time()
     b = pkg.MicrocircuitBatch(cfgs, stream=stream)
     build_s = time.time() - t_build
@@ -368,16 +386,7 @@ def run_batch(args):
     ev1 = sum(b.counters(k)["events"] for k in range(len(b)))
     total_ms = starts[0].elapsed_time(ends[-1])
     events = ev1 - ev0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        e = torch.tensor([float(events)], device=dev, dtype=torch.float64)
-        dist.all_reduce(e)
-        events_all = float(e.item())
-    else:
-        events_all = float(events)
+    total_ms, events_all = reduce_over_ranks(total_ms, events, dev)
     bio_s = args.steps * chunk * 1e-4
     launches_per_step = chunk // info["graph_steps"] + (1 if chunk % info["graph_steps"] else 0)
     avg_launch_s = total_ms * 1e-3 / (args.steps * launches_per_step)
@@ -389,14 +398,15 @@ def run_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/i32",
         "data": "synthetic", "real_time_factor": total_ms * 1e-3 / bio_s,
-        "config": {"workload": "64 independent microcircuits, scales U(0.05, 0.25) (seed 7), "
+        "config": {"workload": "%d independent microcircuits, scales U(0.05, 0.25) (seed 7), "
                                "%d neurons in total, one persistent kernel per graph replay of "
                                "%d time steps; 1 step = %d time steps of every instance"
-                               % (info["n_neurons_total"], info["graph_steps"], chunk),
+                               % (len(b), info["n_neurons_total"], info["graph_steps"], chunk),
                    "time_steps_per_step": chunk, "instances": len(b),
                    "tilings": {"warp_per_spike": tilings.count(0),
                                "block_per_row": tilings.count(1), "flat": tilings.count(2)},
-                   "l2": "no flush: the 64 instances' synapse rows and ring buffers exceed L2",
+                   "l2": "no flush: the instances' synapse rows (%.2f GB) exceed L2"
+                         % (sum(b.info(k)["n_synapses"] for k in range(len(b))) * 4 / 1e9),
                    "parallelism": "replicas" if ws > 1 else "single"},
         "us_per_time_step": total_ms * 1e3 / (args.steps * chunk),
         "events_per_time_step": events / (args.steps * chunk),
@@ -429,12 +439,15 @@ def run_deliver(args):
     hbm_peak, peak_kind = load_peaks()
     rows = []
     rng = np.random.default_rng(99)
-    for scale in (1.0, 4.0):
+    scales = [float(x) for x in args.deliver_scale.split(",")]
+    sizes = [int(x) for x in args.deliver_spikes.split(",")]
+    tilings = [int(x) for x in args.deliver_tilings.split(",")]
+    for scale in scales:
         net = pkg.Microcircuit(workload.microcircuit(scale), stream=stream)
         rp, _, _ = net.export_network(rows_only=True)
         row_len = np.diff(rp.astype(np.int64))
-        for m in (25, 93, 4000, 20000):
-            for tiling in (0, 1, 2):
+        for m in sizes:
+            for tiling in tilings:
                 # pool of lists: at least 1 GB of rows in total, 8 lists minimum
                 per_list = float(row_len.mean()) * 4 * m
                 n_lists = int(min(256, max(8, np.ceil(1.0e9 / per_list))))
@@ -442,8 +455,16 @@ def run_deliver(args):
                          for _ in range(n_lists)]
                 dev = [torch.from_numpy(x).cuda() for x in lists]
                 events = [int(row_len[x].sum()) for x in lists]
-                for k in range(min(3, n_lists)):                 # warm-up
-                    net.deliver(dev[k].data_ptr(), m, k, tiling)
+                try:                                             # warm-up
+                    for k in range(min(3, n_lists)):
+                        net.deliver(dev[k].data_ptr(), m, k, tiling)
+                except pkg.SnnError as err:
+                    if err.code != pkg.SNN_ERR_UNSUPPORTED:
+                        raise
+                    rows.append({"scale": scale, "spikes": m,
+                                 "tiling": ["warp", "block", "partition", "pwords", "cluster"][tiling],
+                                 "unsupported": str(err)})
+                    continue
                 torch.cuda.synchronize()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -457,11 +478,11 @@ def run_deliver(args):
                 ev = float(np.mean(events[:reps]))
                 gbs = 4.0 * ev / (ms * 1e-3) / 1e9
                 rows.append({"scale": scale, "spikes": m,
-                             "tiling": ["warp", "block", "partition"][tiling],
+                             "tiling": ["warp", "block", "partition", "pwords", "cluster"][tiling],
                              "us": ms * 1e3, "events": ev, "achieved_gbs": gbs,
                              "frac": gbs / hbm_peak})
         net.close()
-    best = max(rows, key=lambda r: r["achieved_gbs"])
+    best = max((r for r in rows if "achieved_gbs" in r), key=lambda r: r["achieved_gbs"])
     line = {
         "metric": "synaptic events/s of the delivery kernels alone (one spike list per launch)",
         "value": best["events"] / (best["us"] * 1e-6), "unit": "synaptic events/s", "n_gpus": 1,
@@ -543,6 +564,10 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4000)
     ap.add_argument("--ref-chunk", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--instances", type=int, default=64, help="instances of --workload batch")
+    ap.add_argument("--deliver-scale", default="1.0,4.0", help="--workload deliver: scales")
+    ap.add_argument("--deliver-spikes", default="25,93,4000,20000", help="--workload deliver: list sizes")
+    ap.add_argument("--deliver-tilings", default="0,1,2,3", help="--workload deliver: tilings (4: clusters)")
     ap.add_argument("--workload", default="full",
                     choices=["full", "scale4", "batch", "grad", "deliver"])
     args = ap.parse_args()

@@ -108,6 +108,8 @@ typedef struct snn_info {
     int32_t shared_bytes;     /* dynamic shared memory of the step kernel */
     int32_t slot_entries;     /* largest per-partition slot stride S_c (8-byte entries) */
     int64_t slot_bytes;       /* device memory of the partition slots */
+    int32_t deliver_clusters_active; /* co-resident 8-CTA clusters of snn_deliver
+                                        tiling 4 (0: not available) */
 } snn_info;
 
 typedef struct snn_net snn_net;
@@ -150,6 +152,16 @@ int snn_create_from_rows(const snn_config* cfg, uint64_t seed, const snn_options
  * raster.  Errors found on the device are reported by snn_sync().
  */
 int snn_step(snn_net* net, int64_t n_steps);
+
+/* snn_record_step_times -- from the next snn_step on, the step kernel
+ * writes the device clock (ns, %globaltimer) at the end of every step t into
+ * times_dev[t - t_first], t_first = the step count at this call, for at most
+ * cap steps.  times_dev is caller-owned device memory (int64[cap]); NULL
+ * stops recording.  Consecutive differences are the wall time of each step:
+ * the paper's real-time criterion is every 0.1 ms step within 0.1 ms
+ * (Sec. 3.1.3, Sec. 4.1).  The first step of a launch also carries the
+ * launch gap. */
+int snn_record_step_times(snn_net* net, int64_t* times_dev, int64_t cap);
 
 /* snn_sync -- wait for the stream; returns SNN_OK, SNN_ERR_TIMEOUT if a
  * barrier wait gave up (state undefined), SNN_ERR_OVERFLOW if the raster
@@ -197,7 +209,12 @@ int snn_export_network(snn_net* net, uint64_t* row_ptr_host, uint32_t* words_hos
  * buffer add).  spikes_dev: device array of n_spikes neuron ids (duplicates
  * allowed).  tiling 0: one warp per spike; 1: one CTA per spike row; 2: one
  * CTA per partition, through the partition slots as in snn_step (the ring
- * slice in shared memory when it fits).
+ * slice in shared memory when it fits); 3: one CTA per partition reading
+ * exactly its segment of each row (the packed words between the partition
+ * offsets), weights and ring slice in shared memory; 4: clusters of 8 CTAs,
+ * one partition's ring slice in each CTA's shared memory, every row read once
+ * per cluster and added through distributed shared memory
+ * (SNN_ERR_UNSUPPORTED when a ring slice and the weight table do not fit).
  * Asynchronous on the network's stream; adds to the existing ring content.
  */
 int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int64_t t,

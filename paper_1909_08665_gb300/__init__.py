@@ -75,7 +75,7 @@ class SnnInfo(C.Structure):
                 ("ring_in_shared", C.c_int32), ("max_part_neurons", C.c_int32),
                 ("n_ref", C.c_int32), ("propagators", C.c_float * 4), ("wext_q", C.c_int32),
                 ("shared_bytes", C.c_int32), ("slot_entries", C.c_int32),
-                ("slot_bytes", C.c_int64)]
+                ("slot_bytes", C.c_int64), ("deliver_clusters_active", C.c_int32)]
 
 
 class SnnNoallocIO(C.Structure):
@@ -101,7 +101,8 @@ NOALLOC_MAX_NEURONS = 131072
 
 EXPORTED = ["snn_create", "snn_create_from_rows", "snn_step", "snn_sync", "snn_read_spikes",
             "snn_raster_size", "snn_read_state", "snn_read_ring", "snn_counters", "snn_get_info",
-            "snn_export_network", "snn_deliver", "snn_step_noalloc", "snn_save_state",
+            "snn_export_network", "snn_deliver", "snn_step_noalloc", "snn_record_step_times",
+            "snn_save_state",
             "snn_load_state", "snn_set_params", "snn_grad_forward", "snn_grad_backward",
             "snn_batch_create",
             "snn_batch_step", "snn_batch_sync", "snn_batch_read_spikes", "snn_batch_read_state",
@@ -138,6 +139,7 @@ def lib():
         L.snn_deliver.argtypes = [vp, vp, C.c_int32, C.c_int64, C.c_int32]
         L.snn_step_noalloc.argtypes = [P(SnnConfig), C.c_uint64, P(SnnNoallocIO), C.c_int64,
                                        C.c_int64, vp]
+        L.snn_record_step_times.argtypes = [vp, vp, C.c_int64]
         L.snn_save_state.argtypes = [vp, vp, C.c_int64, P(C.c_int64)]
         L.snn_load_state.argtypes = [vp, vp, C.c_int64]
         L.snn_set_params.argtypes = [vp, P(C.c_double), C.c_double]
@@ -305,6 +307,12 @@ class Microcircuit:
         s, a, b = C.c_int64(), C.c_uint64(), C.c_uint64()
         _check(lib().snn_counters(self._h, C.byref(s), C.byref(a), C.byref(b)))
         return {"step": s.value, "spikes": a.value, "events": b.value}
+
+    def record_step_times(self, times_dev_ptr: int | None, cap: int = 0):
+        """Device int64 buffer (data_ptr) receiving the clock (ns) at the end
+        of each following step; None stops recording."""
+        _check(lib().snn_record_step_times(self._h, None if times_dev_ptr is None
+                                           else C.c_void_p(int(times_dev_ptr)), int(cap)))
 
     # -- state, parameters, gradient -------------------------------------------
     def save_state(self) -> np.ndarray:

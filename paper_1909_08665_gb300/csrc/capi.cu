@@ -568,6 +568,9 @@ void fill_step_params(const snn_net* net, StepParams* out) {
     sp.pop_spikes = net->d_pop_spikes;
     sp.status = net->d_sync + 4;
     sp.abort_flag = net->d_sync + 5;
+    sp.step_times = net->step_times;
+    sp.st_t0 = net->st_t0;
+    sp.st_cap = net->st_cap;
 }
 
 cudaError_t net_launch(snn_net* net, StepParams& sp, int64_t t0, int64_t n) {
@@ -664,6 +667,14 @@ int snn_step(snn_net* net, int64_t n_steps) {
     fill_step_params(net, &sp);
     CK(net_launch(net, sp, net->step, n_steps));
     net->step += n_steps;
+    return SNN_OK;
+}
+
+int snn_record_step_times(snn_net* net, int64_t* times_dev, int64_t cap) {
+    if (!net || cap < 0 || (times_dev && cap == 0)) return fail(SNN_ERR_INVALID, "bad arguments");
+    net->step_times = reinterpret_cast<long long*>(times_dev);
+    net->st_t0 = net->step;
+    net->st_cap = times_dev ? cap : 0;
     return SNN_OK;
 }
 
@@ -768,6 +779,12 @@ int snn_get_info(snn_net* net, snn_info* info) {
     info->shared_bytes = (int32_t)net->smem;
     info->slot_entries = net->slot_entries;
     info->slot_bytes = (int64_t)(net->slot_total * sizeof(int2));
+    int active = 0;
+    if (deliver_cluster_check(net->ncmax, net->P, &active) != cudaSuccess) {
+        cudaGetLastError();
+        active = 0;
+    }
+    info->deliver_clusters_active = active;
     return SNN_OK;
 }
 
@@ -786,7 +803,7 @@ int snn_export_network(snn_net* net, uint64_t* row_ptr_host, uint32_t* words_hos
 
 int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int64_t t,
                 int32_t tiling) {
-    if (!net || n_spikes < 0 || (n_spikes > 0 && !spikes_dev) || tiling < 0 || tiling > 2)
+    if (!net || n_spikes < 0 || (n_spikes > 0 && !spikes_dev) || tiling < 0 || tiling > 4)
         return fail(SNN_ERR_INVALID, "bad arguments");
     if (tiling == 2) {
         StepParams sp;
@@ -810,7 +827,18 @@ int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int6
     dp.wtab = net->d_wtab;
     dp.ring = net->d_ring;
     dp.counters = net->d_counters;
-    CK(launch_deliver(dp, tiling, net->stream));
+    if (tiling == 4) {
+        int active = 0;
+        if (deliver_cluster_check(net->ncmax, net->P, &active) != cudaSuccess || active < 1) {
+            cudaGetLastError();
+            return fail(SNN_ERR_UNSUPPORTED, "ring slices too large for the cluster delivery");
+        }
+        CK(launch_deliver_cluster(dp, net->stream));
+    } else if (tiling == 3) {
+        CK(launch_deliver_pwords(dp, net->smem_ring, net->stream));
+    } else {
+        CK(launch_deliver(dp, tiling, net->stream));
+    }
     return SNN_OK;
 }
 

@@ -90,6 +90,15 @@ namespace {
 constexpr int kAdjThreads = 512;
 constexpr int kAdjWarps = kAdjThreads / 32;
 constexpr int kAdjUnroll = 8;           // row words per lane in flight
+constexpr int kAdjPopTable = 49152;     // largest network with a shared population table
+
+// population of neuron i from the (ascending) starts s_ps[0..8]: binary search
+__device__ __forceinline__ int pop_of_sorted(const int32_t* s_ps, int32_t i) {
+    int pp = i >= s_ps[4] ? 4 : 0;
+    pp += i >= s_ps[pp + 2] ? 2 : 0;
+    pp += i >= s_ps[pp + 1] ? 1 : 0;
+    return pp;
+}
 
 struct AdjParams {
     int32_t n, n_pop, len, chunk;
@@ -135,65 +144,85 @@ __device__ __forceinline__ float surrogate_slope(float x) {
 // phase; one grid barrier per step separates the lI writes of step t from the
 // row gathers of step t - 1.
 __global__ void __launch_bounds__(kAdjThreads, 1) k_adjoint(const __grid_constant__ AdjParams p) {
-    // dynamic shared memory: row starts of the CTA's rows [chunk + 1] (u64),
-    // then the spike adjoints of the current step [chunk]
-    extern __shared__ unsigned long long s_rs[];
+    // dynamic shared memory: the forward's weights in pA and the base weights
+    // ([8][8][128] each: random lookups stay off the L1 wavefront budget), the
+    // row starts of the CTA's rows [chunk + 1] (u64) and the spike adjoints of
+    // the current step [chunk]
+    extern __shared__ unsigned long long s_dyn[];
+    float* s_wf = reinterpret_cast<float*>(s_dyn);
+    float* s_wb = s_wf + kMaxPop * kMaxPop * kWCodes;
+    unsigned long long* s_rs = reinterpret_cast<unsigned long long*>(s_wb + kMaxPop * kMaxPop * kWCodes);
     float* s_ds = reinterpret_cast<float*>(s_rs + p.chunk + 1);
+    // population of every target neuron (one byte each) when the network is
+    // small enough, else a search over the population starts
+    uint8_t* s_pop = p.n <= kAdjPopTable ? reinterpret_cast<uint8_t*>(s_ds + p.chunk) : nullptr;
+    __shared__ int32_t s_ps[kMaxPop + 1];
     __shared__ volatile uint32_t s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t lo = p.blk[blockIdx.x];
     const int32_t hi = p.blk[blockIdx.x + 1];
     if (tid == 0) s_abort = 0u;
     for (int32_t j = lo + tid; j <= hi; j += kAdjThreads) s_rs[j - lo] = p.row_start[j];
+    if (tid <= kMaxPop) s_ps[tid] = tid == 0 ? 0 : (tid < p.n_pop ? p.pop_start[tid] : 0x7fffffff);
+    if (s_pop)
+        for (int32_t i = tid; i < p.n; i += kAdjThreads)
+            s_pop[i] = (uint8_t)pop_index(p.pop_start, p.n_pop, i);
+    const uint32_t n32 = (uint32_t)p.n;
+    for (int k = tid; k < kMaxPop * kMaxPop * kWCodes; k += kAdjThreads) {
+        s_wf[k] = __fmul_rn(__int2float_rn(__ldg(&p.wtab[k])), 0.00390625f);
+        s_wb[k] = __ldg(&p.wbase[k]);
+    }
     __syncthreads();
     const size_t n = (size_t)p.n;
     uint32_t gen = 0;
     for (int s = p.len - 1; s >= 0; --s) {
         const int64_t t = p.t_first + s;
+        const uint32_t t32 = (uint32_t)t;                 // only t mod 64 is used
         const uint8_t* fl = p.tr_f + (size_t)s * n;
         // ---- spike adjoints: loss term plus the rows' pull from lI(t + d) ----
         for (int32_t r = lo + warp; r < hi; r += kAdjWarps) {
             const int32_t j = __ldg(&p.order[r]);
             const int q = pop_index(p.pop_start, p.n_pop, j);
             const bool spk = (fl[j] & 1u) != 0u;
-            int32_t ps[kMaxPop];
-#pragma unroll
-            for (int k = 1; k < kMaxPop; ++k) ps[k] = k < p.n_pop ? p.pop_start[k] : 0x7fffffff;
-            const int32_t* wq = p.wtab + q * kWCodes;
-            const float* bq = p.wbase + q * kWCodes;
+            const float* wq = s_wf + q * kWCodes;
+            const float* bq = s_wb + q * kWCodes;
             float acc = 0.f;
             float pa[kMaxPop];
 #pragma unroll
             for (int k = 0; k < kMaxPop; ++k) pa[k] = 0.f;
-            const unsigned long long b = s_rs[j - lo], e = s_rs[j - lo + 1];
+            const unsigned long long b = s_rs[j - lo];
+            const uint32_t len = (uint32_t)(s_rs[j - lo + 1] - b);
+            const uint32_t* rw = p.words + b;
             // kAdjUnroll words per lane in flight: all word loads, then all
-            // lI and weight loads, then the (fixed-order) accumulation
-            for (unsigned long long base = b + lane; base < e; base += 32ull * kAdjUnroll) {
+            // lI and weight loads, then the (fixed-order) accumulation; the
+            // row-relative offsets, ring index and population lookup are 32-bit
+            for (uint32_t o = (uint32_t)lane; o < len; o += 32u * kAdjUnroll) {
                 uint32_t word[kAdjUnroll];
 #pragma unroll
                 for (int u = 0; u < kAdjUnroll; ++u) {
-                    const unsigned long long w = base + 32ull * u;
-                    word[u] = w < e ? __ldg(&p.words[w]) : 0u;
+                    const uint32_t w = o + 32u * (uint32_t)u;
+                    word[u] = w < len ? __ldg(&rw[w]) : 0u;
                 }
                 float l[kAdjUnroll];
                 int idx[kAdjUnroll];
 #pragma unroll
                 for (int u = 0; u < kAdjUnroll; ++u) {
-                    const int32_t tgt = (int32_t)(word[u] & kTgtMask);
-                    int pp = 0;
-#pragma unroll
-                    for (int k = 1; k < kMaxPop; ++k) pp += tgt >= ps[k] ? 1 : 0;
+                    const uint32_t tgt = word[u] & kTgtMask;
+                    const int pp = s_pop ? (int)s_pop[tgt] : pop_of_sorted(s_ps, (int32_t)tgt);
                     idx[u] = pp * (kMaxPop * kWCodes) + (int)(word[u] >> 25);
-                    const uint32_t slot = (uint32_t)(t + ((word[u] >> kTgtBits) & 63u)) & (kRing - 1);
-                    l[u] = base + 32ull * u < e ? __ldcg(&p.lring[(size_t)slot * n + tgt]) : 0.f;
+                    const uint32_t slot = (t32 + ((word[u] >> kTgtBits) & 63u)) & (kRing - 1);
+                    l[u] = o + 32u * (uint32_t)u < len ? __ldcg(&p.lring[slot * n32 + tgt]) : 0.f;
                 }
+                if (!spk) {
 #pragma unroll
-                for (int u = 0; u < kAdjUnroll; ++u) {
-                    if (base + 32ull * u < e) {
-                        const float wt = __fmul_rn(__int2float_rn(__ldg(&wq[idx[u]])), 0.00390625f);
-                        acc = __fadd_rn(acc, __fmul_rn(wt, l[u]));
-                        if (spk) {
-                            const float v = __fmul_rn(__ldg(&bq[idx[u]]), l[u]);
+                    for (int u = 0; u < kAdjUnroll; ++u)
+                        if (o + 32u * (uint32_t)u < len) acc = __fadd_rn(acc, __fmul_rn(wq[idx[u]], l[u]));
+                } else {
+#pragma unroll
+                    for (int u = 0; u < kAdjUnroll; ++u) {
+                        if (o + 32u * (uint32_t)u < len) {
+                            acc = __fadd_rn(acc, __fmul_rn(wq[idx[u]], l[u]));
+                            const float v = __fmul_rn(bq[idx[u]], l[u]);
                             const int pp = idx[u] / (kMaxPop * kWCodes);
 #pragma unroll
                             for (int k = 0; k < kMaxPop; ++k) pa[k] = __fadd_rn(pa[k], k == pp ? v : 0.f);
@@ -534,7 +563,9 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
     ap.barrier = g->sync;
     ap.status = g->sync + 1;
     ap.abort_flag = g->sync + 2;
-    const size_t smem = sizeof(unsigned long long) * ((size_t)ap.chunk + 1) + sizeof(float) * (size_t)ap.chunk;
+    const size_t smem = 2 * sizeof(float) * kMaxPop * kMaxPop * kWCodes +
+                        sizeof(unsigned long long) * ((size_t)ap.chunk + 1) + sizeof(float) * (size_t)ap.chunk +
+                        (n <= kAdjPopTable ? (size_t)n : 0);
     GCK(cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
 
     StepParams sp;

@@ -59,6 +59,8 @@ struct snn_net {
     uint32_t* d_sync = nullptr;   // [4] status, [5] abort
     unsigned long long* d_pop_spikes = nullptr;   // [8] spikes per population
     snn_grad* grad = nullptr;     // gradient checkpoints and adjoint state
+    long long* step_times = nullptr;  // caller's device buffer of step-end clocks
+    int64_t st_t0 = 0, st_cap = 0;
 };
 
 namespace snn {

@@ -181,6 +181,10 @@ struct StepParams {
     uint8_t* tr_f;
     int64_t tr_t0;
     int32_t tr_len;
+    // optional device clock (ns) at the end of step t, written by CTA 0 to
+    // step_times[t - st_t0] for t - st_t0 in [0, st_cap)
+    long long* step_times;
+    int64_t st_t0, st_cap;
 };
 
 struct DeliverParams {
@@ -229,6 +233,13 @@ cudaError_t step_kernel_configure(int npt, bool smem_ring, size_t smem);
 cudaError_t launch_step(const StepParams& sp, int npt, bool smem_ring, size_t smem,
                         cudaStream_t s);
 cudaError_t launch_deliver(const DeliverParams& dp, int tiling, cudaStream_t s);
+// stand-alone delivery of the exact row segments of each partition (one CTA
+// per partition, packed words, weight table and ring slice in shared memory)
+cudaError_t launch_deliver_pwords(const DeliverParams& dp, bool smem_ring, cudaStream_t s);
+// stand-alone delivery through clusters of 8 CTAs (rings in distributed
+// shared memory); needs the ring slice and the weight table in shared memory
+cudaError_t launch_deliver_cluster(const DeliverParams& dp, cudaStream_t s);
+cudaError_t deliver_cluster_check(int ncmax, int n_part, int* max_active_clusters);
 // stand-alone delivery through the partition slots (one CTA per partition)
 cudaError_t launch_deliver_part(const StepParams& sp, const uint32_t* spikes, int n, int64_t t,
                                 bool smem_ring, cudaStream_t s);

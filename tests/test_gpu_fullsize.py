@@ -68,7 +68,7 @@ def test_full_size_raster_bit_exact_100_steps(full):
 def test_full_size_delivery_both_tilings(full):
     cfg, net = full
     onet = oracle.Network(cfg, n_threads=os.cpu_count())
-    for tiling in (0, 1, 2):
+    for tiling in (0, 1, 2, 3, 4):
         fresh = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
         spikes = workload.random_spike_list(fresh.n, 4000, seed=11 + tiling)
         d = torch.from_numpy(spikes.astype(np.int32)).cuda()
@@ -115,3 +115,32 @@ def test_statistics_agree_across_seeds():
         mean, sd = ref.mean(axis=0), ref.std(axis=0, ddof=1)
         tol = np.maximum(4.0 * sd, 0.15 * np.abs(mean) + 0.02)
         assert np.all(np.abs(g[k] - mean) <= tol), (name, g[k], mean, tol)
+
+
+def test_scale4_short_run_bit_exact():
+    """The 4x network (308,676 neurons, ~1.2e9 synapses, same in-degrees):
+    ring buffers in global memory and 4 neurons per thread, the launch shape
+    the scale-up benchmark times; 30 steps bit for bit against the oracle."""
+    cfg = workload.microcircuit(4.0)
+    net = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
+    info = net.info()
+    assert info["ring_in_shared"] == 0 and info["neurons_per_thread"] == 4
+    assert abs(info["n_synapses"] / 1.2e9 - 1.0) < 0.01
+    steps = 30
+    net.step(steps)
+    net.sync()
+    g = net.read_spikes()
+    g_u, g_i, g_r = net.state()
+    c = net.counters()
+    net.close()
+    sim = oracle.Simulation(oracle.Network(cfg, n_threads=os.cpu_count()))
+    sim.run(steps)
+    o = sim.raster()
+    assert o[0].size > 100
+    np.testing.assert_array_equal(g[0], o[0])
+    np.testing.assert_array_equal(g[1], o[1])
+    o_u, o_i, o_r, _ = sim.state()
+    np.testing.assert_array_equal(g_u.view(np.uint32), o_u.view(np.uint32))
+    np.testing.assert_array_equal(g_i.view(np.uint32), o_i.view(np.uint32))
+    np.testing.assert_array_equal(g_r, o_r)
+    assert c["events"] == sim.counters()["events"]

@@ -197,7 +197,7 @@ def test_empty_network_and_zero_steps():
 # standalone delivery: every tiling against the oracle
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("n_spikes", [1, 25, 93, 4000])
-@pytest.mark.parametrize("tiling", [0, 1, 2])
+@pytest.mark.parametrize("tiling", [0, 1, 2, 3, 4])
 def test_deliver_matches_oracle(cfg01, onet01, n_spikes, tiling):
     net = gpu_net(cfg01)
     spikes = workload.random_spike_list(net.n, n_spikes, seed=n_spikes)
@@ -210,16 +210,41 @@ def test_deliver_matches_oracle(cfg01, onet01, n_spikes, tiling):
     np.testing.assert_array_equal(net.ring(), ref.astype(np.int32))
 
 
-def test_deliver_partition_tiling_with_global_ring(cfg01, onet01):
+def test_deliver_partition_tilings_with_global_ring(cfg01, onet01):
     """Two partitions of 3,859 neurons: the ring does not fit in shared memory
     and the partition tiling accumulates into global memory."""
-    net = gpu_net(cfg01, n_part=2)
-    assert net.info()["ring_in_shared"] == 0
-    spikes = workload.random_spike_list(net.n, 500, seed=3)
+    spikes = workload.random_spike_list(7717, 500, seed=3)
     d = torch.from_numpy(spikes.astype(np.int32)).cuda()
-    net.deliver(d.data_ptr(), spikes.size, 77, 2)
+    ref = onet01.deliver(spikes.astype(np.int32), 77).astype(np.int32)
+    for tiling in (2, 3):
+        net = gpu_net(cfg01, n_part=2)
+        assert net.info()["ring_in_shared"] == 0
+        net.deliver(d.data_ptr(), spikes.size, 77, tiling)
+        net.sync()
+        np.testing.assert_array_equal(net.ring(), ref)
+        net.close()
+    net = gpu_net(cfg01, n_part=2)               # ring slices too large for clusters
+    with pytest.raises(pkg.SnnError) as e:
+        net.deliver(d.data_ptr(), spikes.size, 77, 4)
+    assert e.value.code == pkg.SNN_ERR_UNSUPPORTED
+
+
+def test_step_times_are_recorded(cfg01):
+    net = gpu_net(cfg01)
+    net.step(5)
+    buf = torch.zeros(300, dtype=torch.int64, device="cuda")
+    net.record_step_times(buf.data_ptr(), 250)
+    net.step(120)
+    net.step(200)                    # the recording stops after 250 steps
+    net.record_step_times(None)
+    net.step(10)
     net.sync()
-    np.testing.assert_array_equal(net.ring(), onet01.deliver(spikes.astype(np.int32), 77).astype(np.int32))
+    t = buf.cpu().numpy()
+    assert np.all(t[:250] > 0) and np.all(t[250:] == 0)
+    # the device clock never runs backwards (its tick may exceed one step)
+    assert np.all(np.diff(t[:250]) >= 0) and t[249] > t[0]
+    with pytest.raises(pkg.SnnError):
+        net.record_step_times(buf.data_ptr(), 0)
 
 
 # ---------------------------------------------------------------------------
