@@ -462,7 +462,7 @@ def run_deliver(args):
                     if err.code != pkg.SNN_ERR_UNSUPPORTED:
                         raise
                     rows.append({"scale": scale, "spikes": m,
-                                 "tiling": ["warp", "block", "partition", "pwords", "cluster"][tiling],
+                                 "tiling": ["warp", "block", "partition", "words", "cluster"][tiling],
                                  "unsupported": str(err)})
                     continue
                 torch.cuda.synchronize()
@@ -478,7 +478,7 @@ def run_deliver(args):
                 ev = float(np.mean(events[:reps]))
                 gbs = 4.0 * ev / (ms * 1e-3) / 1e9
                 rows.append({"scale": scale, "spikes": m,
-                             "tiling": ["warp", "block", "partition", "pwords", "cluster"][tiling],
+                             "tiling": ["warp", "block", "partition", "words", "cluster"][tiling],
                              "us": ms * 1e3, "events": ev, "achieved_gbs": gbs,
                              "frac": gbs / hbm_peak})
         net.close()

@@ -210,8 +210,12 @@ int snn_export_network(snn_net* net, uint64_t* row_ptr_host, uint32_t* words_hos
  * allowed).  tiling 0: one warp per spike; 1: one CTA per spike row; 2: one
  * CTA per partition, through the partition slots as in snn_step (the ring
  * slice in shared memory when it fits); 3: one CTA per partition reading
- * exactly its segment of each row (the packed words between the partition
- * offsets), weights and ring slice in shared memory; 4: clusters of 8 CTAs,
+ * exactly its segment of each row (the entries between the partition
+ * offsets), the weights and, when it fits, the ring slice in shared memory;
+ * it reads a pre-decoded copy of the rows (4 bytes per synapse, weight-table
+ * index and ring-cell offset), allocated and built on its first use (its
+ * 19-bit offsets cover 64 slots of the largest partition a network can have);
+ * 4: clusters of 8 CTAs,
  * one partition's ring slice in each CTA's shared memory, every row read once
  * per cluster and added through distributed shared memory
  * (SNN_ERR_UNSUPPORTED when a ring slice and the weight table do not fit).

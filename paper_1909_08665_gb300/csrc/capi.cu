@@ -184,7 +184,7 @@ int make_tables(snn_net* net) {
 
 void free_net(snn_net* net) {
     if (!net) return;
-    void* ptrs[] = {net->d_part_lo, net->d_row_start, net->d_seg, net->d_words, net->d_wtab,
+    void* ptrs[] = {net->d_part_lo, net->d_row_start, net->d_seg, net->d_words, net->d_pre, net->d_wtab,
                     net->d_dtab, net->d_u, net->d_i, net->d_r, net->d_ring, net->d_msg, net->d_slots,
                     net->d_slot_base, net->d_slot_S,
                     net->d_ras_step, net->d_ras_id, net->d_ras_n,
@@ -835,7 +835,14 @@ int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int6
         }
         CK(launch_deliver_cluster(dp, net->stream));
     } else if (tiling == 3) {
-        CK(launch_deliver_pwords(dp, net->smem_ring, net->stream));
+        if (!net->d_pre) {          // pre-decoded rows, built on first use
+            if ((long long)kRing * net->ncmax >= (long long)kPreOffMask)
+                return fail(SNN_ERR_UNSUPPORTED, "ring slices too large for the partition-word delivery");
+            CALL(dalloc(&net->d_pre, (size_t)net->nnz + 4, "pre-decoded rows"));
+            CK(launch_predecode(dp, net->d_row_start, net->d_pre, net->stream));
+        }
+        dp.pre = net->d_pre;
+        CK(launch_deliver_words(dp, net->stream));
     } else {
         CK(launch_deliver(dp, tiling, net->stream));
     }

@@ -39,6 +39,7 @@ struct snn_net {
     unsigned long long* d_row_start = nullptr;
     uint32_t* d_seg = nullptr;
     uint32_t* d_words = nullptr;
+    uint32_t* d_pre = nullptr;              // rows pre-decoded for the partition-word delivery (first use)
     int32_t* d_wtab = nullptr;
     uint8_t* d_dtab = nullptr;
     float* d_u = nullptr;

@@ -195,6 +195,7 @@ struct DeliverParams {
     const int32_t* part_lo;
     const uint32_t* seg;
     const uint32_t* words;
+    const uint32_t* pre;          // pre-decoded rows (partition-word delivery)
     const int32_t* wtab;
     int32_t* ring;
     unsigned long long* counters;
@@ -234,8 +235,16 @@ cudaError_t launch_step(const StepParams& sp, int npt, bool smem_ring, size_t sm
                         cudaStream_t s);
 cudaError_t launch_deliver(const DeliverParams& dp, int tiling, cudaStream_t s);
 // stand-alone delivery of the exact row segments of each partition (one CTA
-// per partition, packed words, weight table and ring slice in shared memory)
-cudaError_t launch_deliver_pwords(const DeliverParams& dp, bool smem_ring, cudaStream_t s);
+// per partition, packed words cut into units of <= 32 words, weight table and,
+// when it fits, the ring slice in shared memory)
+cudaError_t launch_deliver_words(const DeliverParams& dp, cudaStream_t s);
+// pre-decoded rows for launch_deliver_words: entry k of row j is
+// (weight-table index << kPreOffBits) | (delay * ncmax + target - partition start),
+// same layout as the packed words; needs kRing * ncmax < 2^kPreOffBits
+constexpr uint32_t kPreOffBits = 19;
+constexpr uint32_t kPreOffMask = (1u << kPreOffBits) - 1u;
+cudaError_t launch_predecode(const DeliverParams& dp, const unsigned long long* row_start,
+                             uint32_t* pre, cudaStream_t s);
 // stand-alone delivery through clusters of 8 CTAs (rings in distributed
 // shared memory); needs the ring slice and the weight table in shared memory
 cudaError_t launch_deliver_cluster(const DeliverParams& dp, cudaStream_t s);

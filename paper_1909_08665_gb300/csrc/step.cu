@@ -647,98 +647,6 @@ cudaError_t launch_deliver_part(const StepParams& sp, const uint32_t* spikes, in
     return cudaGetLastError();
 }
 
-// Partition-words tiling of the stand-alone delivery: CTA c reads, for every
-// spike, exactly the segment of its row that targets partition c (the packed
-// 4-byte words between seg[j][c] and seg[j][c + 1]: the algorithmic bytes and
-// no more), looks the weight up in a shared copy of the table and adds into
-// its ring slice in shared memory.  A warp takes 32 spikes at a time: their
-// segment bounds in one round trip, then the words of 16 segments in flight.
-template <bool SMEM_RING>
-__global__ void __launch_bounds__(kStepThreads, 1)
-k_deliver_pwords(const __grid_constant__ DeliverParams dp) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    int32_t* s_wt = reinterpret_cast<int32_t*>(smem);
-    const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int R = kRing * dp.ncmax;
-    const int32_t lo = (int32_t)(((long long)c * dp.n) / dp.n_part);
-    int32_t* ring_g = dp.ring + (size_t)c * R;
-    int32_t* ring = SMEM_RING ? reinterpret_cast<int32_t*>(smem + kMaxPop * kMaxPop * kWCodes * 4)
-                              : ring_g;
-    for (int k = tid; k < kMaxPop * kMaxPop * kWCodes; k += kStepThreads) s_wt[k] = __ldg(&dp.wtab[k]);
-    if (SMEM_RING)
-        for (int k = tid; k < R; k += kStepThreads) ring[k] = ring_g[k];
-    __syncthreads();
-    const int32_t base_t = (int32_t)(((uint32_t)dp.t & (kRing - 1)) * (uint32_t)dp.ncmax);
-    int32_t ps[kMaxPop];
-#pragma unroll
-    for (int k = 1; k < kMaxPop; ++k) ps[k] = k < dp.n_pop ? dp.pop_start[k] : 0x7fffffff;
-    unsigned long long events = 0;
-    const int n = dp.n_spikes;
-    // one word of partition c's segment: weight from the shared table of the
-    // row's source population, added at ring slot t + delay
-    auto add = [&](uint32_t x, const int32_t* wq) {
-        const int32_t tgt = (int32_t)(x & kTgtMask);
-        int pp = 0;
-#pragma unroll
-        for (int m = 1; m < kMaxPop; ++m) pp += tgt >= ps[m] ? 1 : 0;
-        int32_t a = base_t + (int32_t)(((x >> kTgtBits) & 63u) * (uint32_t)dp.ncmax) + (tgt - lo);
-        a -= a >= R ? R : 0;
-        atomicAdd(&ring[a], wq[pp * (kMaxPop * kWCodes) + (int)(x >> 25)]);
-    };
-    // 32 spikes per warp round: lane k loads the segment bounds of spike k,
-    // then the first 32 words of 16 segments at a time are in flight
-    for (int g0 = warp * 32; g0 < n; g0 += kWarps * 32) {
-        uint32_t myb = 0u, mye = 0u;
-        int myq = 0;
-        if (g0 + lane < n) {
-            const uint32_t j = __ldg(&dp.spikes[g0 + lane]);
-            const uint32_t* sg = dp.seg + (size_t)j * (size_t)(dp.n_part + 1) + c;
-            myb = __ldg(sg);
-            mye = __ldg(sg + 1);
-            myq = pop_index(dp.pop_start, dp.n_pop, (int32_t)j);
-        }
-#pragma unroll 1
-        for (int h0 = 0; h0 < 32; h0 += 16) {
-            uint32_t w[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const uint32_t b = __shfl_sync(0xffffffffu, myb, h0 + k);
-                const uint32_t e = __shfl_sync(0xffffffffu, mye, h0 + k);
-                w[k] = b + (uint32_t)lane < e ? __ldg(&dp.words[b + lane]) : 0u;
-            }
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const uint32_t b = __shfl_sync(0xffffffffu, myb, h0 + k);
-                const uint32_t e = __shfl_sync(0xffffffffu, mye, h0 + k);
-                const int32_t* wq = s_wt + __shfl_sync(0xffffffffu, myq, h0 + k) * kWCodes;
-                if (b + (uint32_t)lane < e) add(w[k], wq);
-                for (uint32_t x0 = b + 32u + (uint32_t)lane; x0 < e; x0 += 32u)
-                    add(__ldg(&dp.words[x0]), wq);
-                if (lane == 0) events += e - b;
-            }
-        }
-    }
-    __syncthreads();
-    if (SMEM_RING)
-        for (int k = tid; k < R; k += kStepThreads) ring_g[k] = ring[k];
-    if (lane == 0 && events) atomicAdd(&dp.counters[1], events);
-}
-
-cudaError_t launch_deliver_pwords(const DeliverParams& dp, bool smem_ring, cudaStream_t s) {
-    if (dp.n_spikes <= 0) return cudaSuccess;
-    const size_t smem = (size_t)kMaxPop * kMaxPop * kWCodes * 4 +
-                        (smem_ring ? (size_t)kRing * dp.ncmax * 4 : 0);
-    const void* fn = smem_ring ? reinterpret_cast<const void*>(&k_deliver_pwords<true>)
-                               : reinterpret_cast<const void*>(&k_deliver_pwords<false>);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (smem_ring)
-        k_deliver_pwords<true><<<dp.n_part, kStepThreads, smem, s>>>(dp);
-    else
-        k_deliver_pwords<false><<<dp.n_part, kStepThreads, smem, s>>>(dp);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_deliver(const DeliverParams& dp, int tiling, cudaStream_t s) {
     if (dp.n_spikes <= 0) return cudaSuccess;
     if (tiling == 0) {

@@ -133,7 +133,8 @@ def test_scale4_short_run_bit_exact():
     g_u, g_i, g_r = net.state()
     c = net.counters()
     net.close()
-    sim = oracle.Simulation(oracle.Network(cfg, n_threads=os.cpu_count()))
+    onet = oracle.Network(cfg, n_threads=os.cpu_count())
+    sim = oracle.Simulation(onet)
     sim.run(steps)
     o = sim.raster()
     assert o[0].size > 100
@@ -144,3 +145,14 @@ def test_scale4_short_run_bit_exact():
     np.testing.assert_array_equal(g_i.view(np.uint32), o_i.view(np.uint32))
     np.testing.assert_array_equal(g_r, o_r)
     assert c["events"] == sim.counters()["events"]
+    # stand-alone delivery into ring slices in global memory, with every
+    # partition inside at most two populations
+    spikes = workload.random_spike_list(info["n_neurons"], 4000, seed=44).astype(np.int32)
+    ref = onet.deliver(spikes, 4321).astype(np.int32)
+    d = torch.from_numpy(spikes).cuda()
+    for tiling in (1, 3):
+        fresh = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
+        fresh.deliver(d.data_ptr(), spikes.size, 4321, tiling)
+        fresh.sync()
+        np.testing.assert_array_equal(fresh.ring(), ref)
+        fresh.close()
