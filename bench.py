@@ -51,6 +51,10 @@ BYTES_PER_EVENT = 4                   # one packed synaptic word read per event
 # from one ncu capture of this kernel (profiles/k_step_full_microcircuit_dram.md);
 # None for any other workload, and to be re-measured whenever k_step changes
 K_STEP_DRAM_BYTES_PER_STEP_FULL = (14162123008 + 4550912) / 2000.0
+# k_deliver_words, 20,000-spike lists at scale 1: ncu dram__bytes_read + write
+# of three launches (profiles/k_deliver_words_20000_spikes_dram.md) over their
+# mean synaptic events
+K_DELIVER_WORDS_DRAM_BYTES_PER_EVENT = (348.83e6 + 348.71e6 + 348.51e6) / 3.0 / 77.78e6
 
 
 def load_peaks():
@@ -491,7 +495,10 @@ def run_deliver(args):
         "config": {"workload": "snn_deliver of random spike lists at scales 1 and 4; lists drawn "
                                "from pools of >= 1 GB of rows (no list repeats within a timing)"},
         "roofline": {"bound": "hbm", "achieved": best["achieved_gbs"], "peak": hbm_peak,
-                     "unit": "GB/s", "frac": best["frac"], "traffic": None,
+                     "unit": "GB/s", "frac": best["frac"],
+                     "traffic": (K_DELIVER_WORDS_DRAM_BYTES_PER_EVENT * best["events"]
+                                 if best["tiling"] == "words" and best["scale"] == 1.0
+                                 and best["spikes"] == 20000 else None),
                      "peak_kind": peak_kind, "kernel": "k_deliver_%s" % best["tiling"]},
         "cases": rows,
     }
@@ -546,7 +553,10 @@ def run_grad(args):
                    "l2": "not flushed; wall-clock per gradient including host marshalling"},
         "loss": loss, "grad_abs_max": float(gs.abs().max()), "grad_nu": float(gn),
         "clocks": clk.summary(),
-        "gpu_launches": None,
+        # per gradient: the slot rebuild of snn_set_params, one k_step per
+        # checkpoint segment forward, k_step + k_adjoint per segment backward,
+        # and the final k_grad_reduce
+        "gpu_launches": args.steps * (1 + 3 * ((n_steps + every - 1) // every) + 1),
     }
     print(json.dumps(line), flush=True)
 

@@ -39,7 +39,7 @@ constexpr int kWThreads = 1024;
 constexpr int kWWarps = kWThreads / 32;
 constexpr int kRoundSpikes = 64;      // spikes per warp round, two per lane
 constexpr int kBmWords = 64;          // bitmap of segment starts: 2048 positions per window
-constexpr int kChunkBatch = 4;        // chunks of 32 entries per batch; two batches in flight
+constexpr int kChunkBatch = 8;        // chunks of 32 entries per batch; two batches in flight
 constexpr uint32_t kNone = 0xffffffffu;   // no entry (offsets stay below kPreOffMask)
 static_assert(kBmWords % kChunkBatch == 0, "a batch of chunks never crosses a bitmap window");
 
