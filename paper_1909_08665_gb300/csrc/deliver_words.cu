@@ -42,6 +42,7 @@ constexpr int kBmWords = 64;          // bitmap of segment starts: 2048 position
 constexpr int kChunkBatch = 8;        // chunks of 32 entries per batch; two batches in flight
 constexpr uint32_t kNone = 0xffffffffu;   // no entry (offsets stay below kPreOffMask)
 static_assert(kBmWords % kChunkBatch == 0, "a batch of chunks never crosses a bitmap window");
+static_assert(kChunkBatch % 4 == 0, "bitmap words are read four at a time");
 
 // entry p[0] if k < T, else kNone (a predicated load, no branch)
 __device__ __forceinline__ uint32_t load_entry(const uint32_t* p, uint32_t k, uint32_t T) {
@@ -110,8 +111,13 @@ k_deliver_words(const __grid_constant__ DeliverParams dp) {
     const uint32_t ring_s = SMEM_RING ? (uint32_t)__cvta_generic_to_shared(ring) : 0u;
     const uint32_t lanes_le = 0xffffffffu >> (31 - lane);
     const uint32_t lanes_lt = lanes_le >> 1;
+    // rounds of 64 spikes, then kWWarps rounds of 32 for the last spikes of
+    // the list, so that warps run out of work at nearly the same time
     const int n = dp.n_spikes;
-    const int n_rounds = (n + kRoundSpikes - 1) / kRoundSpikes;
+    const int tail = min(n, kWWarps * 32);
+    const int head = n - tail;
+    const int r64 = (head + kRoundSpikes - 1) / kRoundSpikes;
+    const int n_rounds = r64 + (tail + 31) / 32;
     const size_t seg_stride = (size_t)dp.n_part + 1;
     unsigned long long events = 0;
 
@@ -126,11 +132,18 @@ k_deliver_words(const __grid_constant__ DeliverParams dp) {
         b = __ldg(sg);
         len = __ldg(sg + 1) - b;
     };
-    // spike ids of round r for this lane (list positions 64 r + 2 lane, + 1)
+    // spike ids of round r for this lane: list positions 64 r + 2 lane and
+    // + 1 in the first r64 rounds, head + 32 (r - r64) + lane after them
     auto ids = [&](int r, uint32_t& j0, uint32_t& j1) {
-        const int g = r * kRoundSpikes + 2 * lane;
-        j0 = g < n ? __ldg(&dp.spikes[g]) : kNone;
-        j1 = g + 1 < n ? __ldg(&dp.spikes[g + 1]) : kNone;
+        if (r < r64) {
+            const int g = r * kRoundSpikes + 2 * lane;
+            j0 = g < head ? __ldg(&dp.spikes[g]) : kNone;
+            j1 = g + 1 < head ? __ldg(&dp.spikes[g + 1]) : kNone;
+        } else {
+            const int g = head + 32 * (r - r64) + lane;
+            j0 = g < n ? __ldg(&dp.spikes[g]) : kNone;
+            j1 = kNone;
+        }
     };
     auto round_bounds = [&](uint32_t j0, uint32_t j1, uint32_t& b0, uint32_t& l0, uint32_t& b1,
                             uint32_t& l1) {
@@ -188,10 +201,20 @@ k_deliver_words(const __grid_constant__ DeliverParams dp) {
             // window; past T the bitmap is zero and loads and adds are
             // predicated off.
             auto load = [&](uint32_t c0, uint32_t (&e)[kChunkBatch]) {
-                const uint32_t* bmc = bm + ((c0 - w0) >> 5);
+                // the batch's bitmap words, four per broadcast load
+                const uint4* bmv = reinterpret_cast<const uint4*>(bm + ((c0 - w0) >> 5));
+                uint32_t masks[kChunkBatch];
+#pragma unroll
+                for (int v = 0; v < kChunkBatch / 4; ++v) {
+                    const uint4 m = bmv[v];
+                    masks[4 * v] = m.x;
+                    masks[4 * v + 1] = m.y;
+                    masks[4 * v + 2] = m.z;
+                    masks[4 * v + 3] = m.w;
+                }
 #pragma unroll
                 for (int u = 0; u < kChunkBatch; ++u) {
-                    const uint32_t mask = bmc[u];
+                    const uint32_t mask = masks[u];
                     const uint32_t o = rbase + __popc(mask & lanes_le) - 1u;
                     rbase += __popc(mask);
                     const uint32_t k = c0 + 32u * u + (uint32_t)lane;
