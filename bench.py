@@ -29,6 +29,11 @@ Other workloads (--workload; the default line is the full microcircuit):
           100 steps + backward) of the 10 % microcircuit over 200 ms
   deliver the delivery kernels alone on spike lists of 25 / 93 / 4,000 /
           20,000 random sources at scales 1 and 4 (HBM roofline per case)
+  realtime the full microcircuit paced to wall-clock time (one 0.1 ms step per
+          0.1 ms) for --steps biological seconds: deadlines missed, step-end
+          intervals
+  soak    a long run of --steps biological seconds with the raster streamed
+          to the host every second, then a resume-from-checkpoint check
 """
 import argparse
 import json
@@ -505,6 +510,140 @@ def run_deliver(args):
     print(json.dumps(line), flush=True)
 
 
+def run_realtime(args):
+    """True real time (Sec. 4.1): the full microcircuit paced at one 0.1 ms
+    step per 0.1 ms of wall time (snn_set_realtime) for --steps seconds of
+    biological time in one launch, the raster read to the host afterwards.
+    Reports the wall time per biological second, the deadlines missed (a step
+    ending more than 0.1 ms after its release) and the intervals between step
+    ends on the device clock."""
+    import torch
+
+    import paper_1909_08665_gb300 as pkg
+    import workload
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    cfg = workload.microcircuit(args.scale, seed=12345)
+    period_ns = int(round(cfg["dt"] * 1e6))           # dt in ms
+    n = args.steps * STEPS_PER_BENCH_STEP
+    net = pkg.Microcircuit(cfg, stream=stream)
+    for _ in range(args.warmup):                       # unpaced
+        net.step(STEPS_PER_BENCH_STEP)
+    net.sync()
+    pending = max(1, net.raster_size())
+    net.read_spikes_into(np.zeros(pending, np.uint32), np.zeros(pending, np.uint32))
+    clock = torch.zeros(n, dtype=torch.int64, device="cuda")
+    net.record_step_times(clock.data_ptr(), n)
+    net.set_realtime(period_ns)
+    c0 = net.counters()
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        net.step(n)
+        net.sync()
+        wall = time.perf_counter() - t0
+    rt = net.realtime_stats()
+    net.set_realtime(0)
+    net.record_step_times(None)
+    c1 = net.counters()
+    steps_host, ids_host = net.read_spikes()
+    d_us = np.diff(clock.cpu().numpy()) * 1e-3
+    bio_s = n * cfg["dt"] * 1e-3
+    line = {
+        "metric": "wall-clock seconds per biological second, paced at one 0.1 ms step per "
+                  "0.1 ms (true real time, full microcircuit, 1 GB300)",
+        "value": wall / bio_s, "unit": "s/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32/i32",
+        "data": "synthetic",
+        "config": {"workload": "full microcircuit paced to wall-clock time, %d time steps "
+                               "(%g s biological) in one launch" % (n, bio_s),
+                   "scale": args.scale, "period_ns": period_ns,
+                   "l2": "no flush: synapse rows exceed L2"},
+        "deadlines_missed": rt["missed"], "max_lateness_us": rt["max_late_ns"] * 1e-3,
+        "step_end_interval_us": {"median": float(np.median(d_us)), "p01": float(np.percentile(d_us, 1)),
+                                 "p99": float(np.percentile(d_us, 99)), "max": float(d_us.max())},
+        "spikes": int(c1["spikes"] - c0["spikes"]), "spikes_read": int(steps_host.size),
+        "events": int(c1["events"] - c0["events"]),
+        "clocks": clk.summary(),
+        "gpu_launches": 1,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_soak(args):
+    """Long run (the paper reports several 12 h simulations, Sec. 5): the full
+    microcircuit for --steps biological seconds, one second per launch, the
+    raster streamed to pinned host memory after every second and checked
+    against the device's spike count.  Then a resume check: the state saved at
+    the end, one more second simulated, and the same second simulated again by
+    a second network instance that loaded the saved state; the two rasters
+    must be identical."""
+    import torch
+
+    import paper_1909_08665_gb300 as pkg
+    import workload
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    cfg = workload.microcircuit(args.scale, seed=12345)
+    chunk = STEPS_PER_BENCH_STEP
+    net = pkg.Microcircuit(cfg, stream=stream)
+    bounds = np.cumsum([0] + list(cfg["pop_sizes"]))
+    sizes = np.asarray(cfg["pop_sizes"], np.float64)
+    cap = 1 << 24
+    h_steps = torch.empty(cap, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    h_ids = torch.empty(cap, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    counts = np.zeros((args.steps, len(sizes)), np.int64)
+    drained = 0
+    c0 = net.counters()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            net.step(chunk)
+            m = net.read_spikes_into(h_steps, h_ids)
+            drained += m
+            pops = np.searchsorted(bounds, h_ids[:m], side="right") - 1
+            counts[k] = np.bincount(pops, minlength=len(sizes))[:len(sizes)]
+        wall = time.perf_counter() - t0
+    c1 = net.counters()
+    rates = counts / sizes[None, :] / (chunk * cfg["dt"] * 1e-3)
+    # resume from a saved state in a second instance of the network
+    snap = net.save_state()
+    net.step(chunk)
+    a = net.read_spikes()
+    other = pkg.Microcircuit(cfg, stream=stream)
+    other.load_state(snap)
+    other.step(chunk)
+    b = other.read_spikes()
+    resume_ok = bool(a[0].size > 0 and np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]))
+    other.close()
+    net.close()
+    bio_s = args.steps * chunk * cfg["dt"] * 1e-3
+    line = {
+        "metric": "wall-clock seconds per biological second of a long run, raster streamed to "
+                  "the host every biological second (full microcircuit, 1 GB300)",
+        "value": wall / bio_s, "unit": "s/s", "n_gpus": 1, "steps": args.steps, "warmup": 0,
+        "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/i32", "data": "synthetic",
+        "config": {"workload": "full microcircuit, %g s biological, 1 s per launch, raster "
+                               "drained to pinned host memory after every launch" % bio_s,
+                   "scale": args.scale},
+        "spikes_counted": int(c1["spikes"] - c0["spikes"]), "spikes_drained": int(drained),
+        "events": int(c1["events"] - c0["events"]),
+        "rate_hz_mean": [float(x) for x in rates.mean(axis=0)],
+        "total_rate_hz_per_second": {"min": float((counts.sum(1) / sizes.sum()).min()),
+                                     "max": float((counts.sum(1) / sizes.sum()).max())},
+        "resume_bit_identical": resume_ok,
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps + 2,
+        "e2e": {"value": wall / bio_s, "unit": "s/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 8 * drained // max(args.steps, 1)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_grad(args):
     import torch
 
@@ -579,7 +718,7 @@ def main():
     ap.add_argument("--deliver-spikes", default="25,93,4000,20000", help="--workload deliver: list sizes")
     ap.add_argument("--deliver-tilings", default="0,1,2,3", help="--workload deliver: tilings (4: clusters)")
     ap.add_argument("--workload", default="full",
-                    choices=["full", "scale4", "batch", "grad", "deliver"])
+                    choices=["full", "scale4", "batch", "grad", "deliver", "realtime", "soak"])
     args = ap.parse_args()
     if args.workload == "scale4":
         args.scale = 4.0
@@ -591,6 +730,10 @@ def main():
         run_grad(args)
     elif args.workload == "deliver":
         run_deliver(args)
+    elif args.workload == "realtime":
+        run_realtime(args)
+    elif args.workload == "soak":
+        run_soak(args)
     else:
         run_ours(args)
 

@@ -163,6 +163,28 @@ int snn_step(snn_net* net, int64_t n_steps);
  * launch gap. */
 int snn_record_step_times(snn_net* net, int64_t* times_dev, int64_t cap);
 
+/* snn_set_realtime -- pace snn_step to wall-clock time, the paper's "true
+ * real time" (Sec. 4.1: every 0.1 ms step evaluated in 0.1 ms of wall time;
+ * on SpiNNaker a 0.1 ms timer interrupt starts each step, Sec. 3.1.3).  From
+ * the next snn_step on, step t starts no earlier than
+ * anchor + (t - t_a) * period_ns, where t_a is the step count at this call
+ * and anchor is the device clock (%globaltimer) when step t_a starts.  The
+ * schedule is continuous across snn_step calls: a caller that pauses falls
+ * behind it, and the late steps then run unpaced and count as missed until
+ * the schedule is caught up.  A step that ends after its start time plus
+ * period_ns has missed its deadline (measured at the end of the step by CTA
+ * 0); snn_realtime_stats reads the count and the largest lateness.  Each
+ * call resets the statistics and re-anchors; period_ns = 0 turns pacing
+ * off.  period_ns in [0, 1e9], else SNN_ERR_INVALID.  Pacing changes no
+ * result: rasters and state are those of an unpaced run.  Waits are bounded.
+ * Only snn_step is paced (not the gradient or batch entry points). */
+int snn_set_realtime(snn_net* net, int64_t period_ns);
+
+/* snn_realtime_stats -- deadlines missed since the last snn_set_realtime,
+ * and the largest lateness in ns (both 0 when pacing was never enabled).
+ * Synchronises the network's stream. */
+int snn_realtime_stats(snn_net* net, int64_t* missed, int64_t* max_late_ns);
+
 /* snn_sync -- wait for the stream; returns SNN_OK, SNN_ERR_TIMEOUT if a
  * barrier wait gave up (state undefined), SNN_ERR_OVERFLOW if the raster
  * overflowed, or SNN_ERR_CUDA. */

@@ -102,7 +102,7 @@ NOALLOC_MAX_NEURONS = 131072
 EXPORTED = ["snn_create", "snn_create_from_rows", "snn_step", "snn_sync", "snn_read_spikes",
             "snn_raster_size", "snn_read_state", "snn_read_ring", "snn_counters", "snn_get_info",
             "snn_export_network", "snn_deliver", "snn_step_noalloc", "snn_record_step_times",
-            "snn_save_state",
+            "snn_set_realtime", "snn_realtime_stats", "snn_save_state",
             "snn_load_state", "snn_set_params", "snn_grad_forward", "snn_grad_backward",
             "snn_batch_create",
             "snn_batch_step", "snn_batch_sync", "snn_batch_read_spikes", "snn_batch_read_state",
@@ -140,6 +140,8 @@ def lib():
         L.snn_step_noalloc.argtypes = [P(SnnConfig), C.c_uint64, P(SnnNoallocIO), C.c_int64,
                                        C.c_int64, vp]
         L.snn_record_step_times.argtypes = [vp, vp, C.c_int64]
+        L.snn_set_realtime.argtypes = [vp, C.c_int64]
+        L.snn_realtime_stats.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
         L.snn_save_state.argtypes = [vp, vp, C.c_int64, P(C.c_int64)]
         L.snn_load_state.argtypes = [vp, vp, C.c_int64]
         L.snn_set_params.argtypes = [vp, P(C.c_double), C.c_double]
@@ -313,6 +315,17 @@ class Microcircuit:
         of each following step; None stops recording."""
         _check(lib().snn_record_step_times(self._h, None if times_dev_ptr is None
                                            else C.c_void_p(int(times_dev_ptr)), int(cap)))
+
+    def set_realtime(self, period_ns: int):
+        """Pace the following steps to wall-clock time: one step per period_ns
+        (100_000 for the paper's true real time at dt = 0.1 ms); 0 stops."""
+        _check(lib().snn_set_realtime(self._h, int(period_ns)))
+
+    def realtime_stats(self) -> dict:
+        """Deadlines missed since set_realtime and the largest lateness (ns)."""
+        m, late = C.c_int64(), C.c_int64()
+        _check(lib().snn_realtime_stats(self._h, C.byref(m), C.byref(late)))
+        return {"missed": m.value, "max_late_ns": late.value}
 
     # -- state, parameters, gradient -------------------------------------------
     def save_state(self) -> np.ndarray:

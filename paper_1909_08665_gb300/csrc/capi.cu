@@ -188,7 +188,7 @@ void free_net(snn_net* net) {
                     net->d_dtab, net->d_u, net->d_i, net->d_r, net->d_ring, net->d_msg, net->d_slots,
                     net->d_slot_base, net->d_slot_S,
                     net->d_ras_step, net->d_ras_id, net->d_ras_n,
-                    net->d_counters, net->d_sync, net->d_pop_spikes};
+                    net->d_counters, net->d_sync, net->d_pop_spikes, net->d_rt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free_grad(net->grad);
@@ -665,8 +665,37 @@ int snn_step(snn_net* net, int64_t n_steps) {
     if (n_steps < 0) return fail(SNN_ERR_INVALID, "n_steps must be >= 0");
     StepParams sp;
     fill_step_params(net, &sp);
+    if (net->rt_period) {
+        sp.rt_period_ns = net->rt_period;
+        sp.rt_t_anchor = net->rt_t_anchor;
+        sp.rt = net->d_rt;
+    }
     CK(net_launch(net, sp, net->step, n_steps));
     net->step += n_steps;
+    return SNN_OK;
+}
+
+int snn_set_realtime(snn_net* net, int64_t period_ns) {
+    if (!net || period_ns < 0 || period_ns > 1000000000ll)
+        return fail(SNN_ERR_INVALID, "period_ns must be in [0, 1e9]");
+    if (!net->d_rt) CALL(dalloc(&net->d_rt, 3, "pacing state"));
+    CK(cudaStreamSynchronize(net->stream));
+    CK(cudaMemset(net->d_rt, 0, 3 * sizeof(unsigned long long)));
+    net->rt_period = (uint64_t)period_ns;
+    net->rt_t_anchor = net->step;
+    return SNN_OK;
+}
+
+int snn_realtime_stats(snn_net* net, int64_t* missed, int64_t* max_late_ns) {
+    if (!net || !missed || !max_late_ns) return fail(SNN_ERR_INVALID, "bad arguments");
+    *missed = 0;
+    *max_late_ns = 0;
+    if (!net->d_rt) return SNN_OK;
+    unsigned long long h[3];
+    CK(cudaStreamSynchronize(net->stream));
+    CK(cudaMemcpy(h, net->d_rt, sizeof(h), cudaMemcpyDeviceToHost));
+    *missed = (int64_t)h[1];
+    *max_late_ns = (int64_t)h[2];
     return SNN_OK;
 }
 

@@ -59,6 +59,9 @@ struct snn_net {
     unsigned long long* d_counters = nullptr;
     uint32_t* d_sync = nullptr;   // [4] status, [5] abort
     unsigned long long* d_pop_spikes = nullptr;   // [8] spikes per population
+    uint64_t rt_period = 0;                 // pacing period in ns (0: off)
+    int64_t rt_t_anchor = 0;                // step whose start anchors the paced run
+    unsigned long long* d_rt = nullptr;     // [3] anchor, missed deadlines, max lateness
     snn_grad* grad = nullptr;     // gradient checkpoints and adjoint state
     long long* step_times = nullptr;  // caller's device buffer of step-end clocks
     int64_t st_t0 = 0, st_cap = 0;

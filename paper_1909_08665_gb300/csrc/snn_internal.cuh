@@ -72,6 +72,15 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
+// wait until the device clock reaches target; bounded by 2^26 sleeps of
+// about 128 ns (seconds, beyond the longest allowed pacing period)
+__device__ __forceinline__ void wait_until_ns(uint64_t target) {
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (globaltimer_ns() >= target) return;
+        __nanosleep(128);
+    }
+}
+
 // Full grid barrier of a cooperative launch on a monotonic arrival counter
 // (zeroed before the launch): barrier number `gen` completes when the counter
 // reaches (gen + 1) * gridDim.x.  The wait is bounded: it gives up when
@@ -185,6 +194,13 @@ struct StepParams {
     // step_times[t - st_t0] for t - st_t0 in [0, st_cap)
     long long* step_times;
     int64_t st_t0, st_cap;
+    // pacing to wall-clock time (0: off): step t starts no earlier than
+    // rt[0] + (t - rt_t_anchor) * rt_period_ns, rt[0] being the device clock
+    // when the first paced step started (0 until then); rt[1] counts steps
+    // that ended after their deadline, rt[2] holds the largest lateness (ns)
+    unsigned long long rt_period_ns;
+    int64_t rt_t_anchor;
+    unsigned long long* rt;
 };
 
 struct DeliverParams {

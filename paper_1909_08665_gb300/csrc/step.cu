@@ -313,7 +313,9 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
 // ---------------------------------------------------------------------------
 // persistent step kernel
 // ---------------------------------------------------------------------------
-template <int NPT, bool SMEM_RING>
+// PACED: the variant for runs paced to wall-clock time (snn_set_realtime);
+// the pacing code lives only there, so the unpaced step loop is unchanged
+template <int NPT, bool SMEM_RING, bool PACED>
 __global__ void __launch_bounds__(kStepThreads, 1)
 k_step(const __grid_constant__ StepParams sp) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -336,6 +338,10 @@ k_step(const __grid_constant__ StepParams sp) {
     if (SMEM_RING)
         for (int k = tid; k < kRing * sp.ncmax; k += kStepThreads) ring[k] = ring_g[k];
     if (tid < 32) s_misc[tid] = 0u;
+    // pacing to wall-clock time: the first CTA to arrive fixes the anchor of
+    // the paced run (the device clock at which step rt_t_anchor starts) in
+    // rt[0]; the barrier before the step loop orders it before every read
+    if (PACED && tid == 0) atomicCAS(sp.rt, 0ull, globaltimer_ns());
 
     float u[NPT], isyn[NPT];
     int32_t refr[NPT], pacc[NPT];
@@ -361,6 +367,9 @@ k_step(const __grid_constant__ StepParams sp) {
     for (int s = 0; s < sp.n_steps; ++s) {
         const int64_t t = sp.t0 + s;
         const unsigned long long tag = (unsigned long long)(uint32_t)(t + 1) << 32;
+        // paced run: step t is released at anchor + (t - t_anchor) periods
+        if (PACED)
+            wait_until_ns(__ldcg(sp.rt) + (unsigned long long)(t - sp.rt_t_anchor) * sp.rt_period_ns);
         unsigned long long* my_msg = sp.msg + ((size_t)(t & 3) * P + c) * sp.msg_stride;
         uint32_t* my_cnt = &s_misc[s & 1];
         // headers of step t-1 were published one step ago: load them now so
@@ -474,6 +483,17 @@ k_step(const __grid_constant__ StepParams sp) {
             const int64_t r = t - sp.st_t0;
             if (r >= 0 && r < sp.st_cap) sp.step_times[r] = (long long)globaltimer_ns();
         }
+        // paced run: a step that ends after release + period missed its
+        // deadline (CTA 0's view of the step end)
+        if (PACED && c == 0 && tid == 0) {
+            const unsigned long long now = globaltimer_ns();
+            const unsigned long long deadline =
+                __ldcg(sp.rt) + (unsigned long long)(t + 1 - sp.rt_t_anchor) * sp.rt_period_ns;
+            if (now > deadline) {
+                atomicAdd(&sp.rt[1], 1ull);
+                atomicMax(&sp.rt[2], now - deadline);
+            }
+        }
     }
 
     // ---- epilogue: deliver the spikes of the last step ----
@@ -569,35 +589,54 @@ size_t step_shared_bytes(int ncmax, int n_part, bool smem_ring) {
 }
 
 template <int NPT, bool R>
-static const void* step_fn() { return reinterpret_cast<const void*>(&k_step<NPT, R>); }
+static const void* step_fn(bool paced) {
+    return paced ? reinterpret_cast<const void*>(&k_step<NPT, R, true>)
+                 : reinterpret_cast<const void*>(&k_step<NPT, R, false>);
+}
 
-static const void* select_step(int npt, bool smem_ring) {
+static const void* select_step(int npt, bool smem_ring, bool paced) {
     switch (npt) {
-        case 1: return smem_ring ? step_fn<1, true>() : step_fn<1, false>();
-        case 2: return smem_ring ? step_fn<2, true>() : step_fn<2, false>();
-        case 4: return smem_ring ? step_fn<4, true>() : step_fn<4, false>();
-        case 8: return smem_ring ? step_fn<8, true>() : step_fn<8, false>();
+        case 1: return smem_ring ? step_fn<1, true>(paced) : step_fn<1, false>(paced);
+        case 2: return smem_ring ? step_fn<2, true>(paced) : step_fn<2, false>(paced);
+        case 4: return smem_ring ? step_fn<4, true>(paced) : step_fn<4, false>(paced);
+        case 8: return smem_ring ? step_fn<8, true>(paced) : step_fn<8, false>(paced);
         default: return nullptr;
     }
 }
 
-int step_kernel_variant(int npt, bool smem_ring) { return select_step(npt, smem_ring) != nullptr; }
-
-cudaError_t step_kernel_configure(int npt, bool smem_ring, size_t smem) {
-    const void* fn = select_step(npt, smem_ring);
-    if (!fn) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+int step_kernel_variant(int npt, bool smem_ring) {
+    return select_step(npt, smem_ring, false) != nullptr;
 }
 
+cudaError_t step_kernel_configure(int npt, bool smem_ring, size_t smem) {
+    for (int paced = 0; paced < 2; ++paced) {
+        const void* fn = select_step(npt, smem_ring, paced != 0);
+        if (!fn) return cudaErrorInvalidValue;
+        const cudaError_t e =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// co-resident CTAs per SM: the smaller of the two variants' figures
 cudaError_t step_max_blocks(int npt, bool smem_ring, size_t smem, int* blocks_per_sm) {
-    const void* fn = select_step(npt, smem_ring);
-    if (!fn) return cudaErrorInvalidValue;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kStepThreads, smem);
+    int best = 1 << 30;
+    for (int paced = 0; paced < 2; ++paced) {
+        const void* fn = select_step(npt, smem_ring, paced != 0);
+        if (!fn) return cudaErrorInvalidValue;
+        int b = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kStepThreads, smem);
+        if (e != cudaSuccess) return e;
+        best = std::min(best, b);
+    }
+    *blocks_per_sm = best;
+    return cudaSuccess;
 }
 
 cudaError_t launch_step(const StepParams& sp, int npt, bool smem_ring, size_t smem,
                         cudaStream_t s) {
-    const void* fn = select_step(npt, smem_ring);
+    const void* fn = select_step(npt, smem_ring, sp.rt_period_ns != 0ull);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {const_cast<StepParams*>(&sp)};
     return cudaLaunchCooperativeKernel(fn, dim3(sp.n_part), dim3(kStepThreads), args, smem, s);

@@ -4,6 +4,8 @@ The bar is bit-exact: spike rasters (step, id), fp32 membrane potentials and
 synaptic currents (compared as bit patterns), refractory counters, int32 ring
 buffers and the synaptic matrix itself.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -227,6 +229,45 @@ def test_deliver_partition_tilings_with_global_ring(cfg01, onet01):
     with pytest.raises(pkg.SnnError) as e:
         net.deliver(d.data_ptr(), spikes.size, 77, 4)
     assert e.value.code == pkg.SNN_ERR_UNSUPPORTED
+
+
+def test_realtime_pacing_keeps_the_wall_clock_and_the_results(cfg01):
+    """Paced at 0.1 ms per step (the paper's true real time, Sec. 4.1): 2,000
+    steps take 0.2 s of wall time, step ends are 0.1 ms apart, no deadline is
+    missed, and the raster and state are those of an unpaced run."""
+    steps, period = 2000, 100_000
+    ref = gpu_net(cfg01)
+    ref.step(steps)
+    ref.sync()
+    net = gpu_net(cfg01)
+    buf = torch.zeros(steps, dtype=torch.int64, device="cuda")
+    net.record_step_times(buf.data_ptr(), steps)
+    net.set_realtime(period)
+    t0 = time.perf_counter()
+    net.step(steps // 2)
+    net.step(steps - steps // 2)          # the schedule continues across calls
+    net.sync()
+    wall = time.perf_counter() - t0
+    assert (steps - 1) * period * 1e-9 <= wall < steps * period * 1e-9 + 0.5
+    d = np.diff(buf.cpu().numpy())
+    assert abs(np.median(d) - period) < 0.02 * period
+    assert d.min() > 0.5 * period
+    st = net.realtime_stats()
+    assert st["missed"] <= steps // 100, st
+    g, o = net.read_spikes(), ref.read_spikes()
+    np.testing.assert_array_equal(g[0], o[0])
+    np.testing.assert_array_equal(g[1], o[1])
+    for a, b in zip(net.state(), ref.state()):
+        np.testing.assert_array_equal(a, b)
+    net.set_realtime(0)                   # pacing off: fast again
+    t0 = time.perf_counter()
+    net.step(steps)
+    net.sync()
+    assert time.perf_counter() - t0 < 0.1
+    with pytest.raises(pkg.SnnError):
+        net.set_realtime(-1)
+    net.close()
+    ref.close()
 
 
 def test_step_times_are_recorded(cfg01):
