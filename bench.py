@@ -59,7 +59,7 @@ K_STEP_DRAM_BYTES_PER_STEP_FULL = (14162123008 + 4550912) / 2000.0
 # k_deliver_words, 20,000-spike lists at scale 1: ncu dram__bytes_read + write
 # of three launches (profiles/k_deliver_words_20000_spikes_dram.md) over their
 # mean synaptic events
-K_DELIVER_WORDS_DRAM_BYTES_PER_EVENT = (348.83e6 + 348.71e6 + 348.51e6) / 3.0 / 77.78e6
+K_DELIVER_WORDS_DRAM_BYTES_PER_EVENT = (349.75e6 + 348.93e6 + 349.31e6) / 3.0 / 77.78e6
 
 
 def load_peaks():
