@@ -55,7 +55,7 @@ BYTES_PER_EVENT = 4                   # one packed synaptic word read per event
 # DRAM bytes (read + write) per time step of k_step on the full microcircuit,
 # from one ncu capture of this kernel (profiles/k_step_full_microcircuit_dram.md);
 # None for any other workload, and to be re-measured whenever k_step changes
-K_STEP_DRAM_BYTES_PER_STEP_FULL = (14162123008 + 4550912) / 2000.0
+K_STEP_DRAM_BYTES_PER_STEP_FULL = (14161993728 + 4584960) / 2000.0
 # k_deliver_words, 20,000-spike lists at scale 1: ncu dram__bytes_read + write
 # of three launches (profiles/k_deliver_words_20000_spikes_dram.md) over their
 # mean synaptic events
