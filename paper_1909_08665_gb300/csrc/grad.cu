@@ -67,6 +67,7 @@ struct snn_grad {
     int32_t* blk = nullptr;         // [grid + 1] row range of each adjoint CTA
     int32_t* order = nullptr;       // [n] each CTA's rows, longest first
     int32_t grid = 0, chunk = 0;    // CTAs of the adjoint, most rows of one CTA
+    uint32_t* pre = nullptr;        // pre-decoded rows of the adjoint gather (small networks)
 };
 
 namespace snn {
@@ -75,7 +76,7 @@ void free_grad(snn_grad* g) {
     if (!g) return;
     void* ptrs[] = {g->ckpt, g->tr_u, g->tr_f, g->lu, g->lI, g->lring, g->mnext, g->gA, g->gN,
                     g->wbase, g->out, g->sync, g->saved, g->saved_ras, g->saved_status,
-                    g->pop_start, g->blk, g->order};
+                    g->pop_start, g->blk, g->order, g->pre};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -111,6 +112,9 @@ struct AdjParams {
     uint64_t timeout_ns;
     const unsigned long long* row_start;
     const uint32_t* words;
+    // entry k of row j: (weight-table index << kPreOffBits) | (delay * n + target),
+    // the words pre-decoded for the gather (64 n < 2^kPreOffBits)
+    const uint32_t* pre;
     const int32_t* wtab;             // rounded weights of the forward, 1/256 pA
     const float* wbase;
     const float* tr_u;
@@ -142,7 +146,11 @@ __device__ __forceinline__ float surrogate_slope(float x) {
 // blk[b + 1]) (ranges balanced by total row length): their rows in the spike
 // phase, taken by the warps longest first, and their state in the membrane
 // phase; one grid barrier per step separates the lI writes of step t from the
-// row gathers of step t - 1.
+// row gathers of step t - 1.  PRE: the rows are read from the pre-decoded
+// copy (weight-table index and ring offset per synapse), which takes the
+// population lookup and the slot arithmetic off the gather; every value and
+// every sum is the same as in the packed-word path.
+template <bool PRE>
 __global__ void __launch_bounds__(kAdjThreads, 1) k_adjoint(const __grid_constant__ AdjParams p) {
     // dynamic shared memory: the forward's weights in pA and the base weights
     // ([8][8][128] each: random lookups stay off the L1 wavefront budget), the
@@ -184,15 +192,17 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adjoint(const __grid_constan
             const int32_t j = __ldg(&p.order[r]);
             const int q = pop_index(p.pop_start, p.n_pop, j);
             const bool spk = (fl[j] & 1u) != 0u;
-            const float* wq = s_wf + q * kWCodes;
-            const float* bq = s_wb + q * kWCodes;
+            // PRE indexes the whole table [p][q][code]; the packed path the
+            // source population's block [p][code]
+            const float* wq = PRE ? s_wf : s_wf + q * kWCodes;
+            const float* bq = PRE ? s_wb : s_wb + q * kWCodes;
             float acc = 0.f;
             float pa[kMaxPop];
 #pragma unroll
             for (int k = 0; k < kMaxPop; ++k) pa[k] = 0.f;
             const unsigned long long b = s_rs[j - lo];
             const uint32_t len = (uint32_t)(s_rs[j - lo + 1] - b);
-            const uint32_t* rw = p.words + b;
+            const uint32_t* rw = (PRE ? p.pre : p.words) + b;
             // kAdjUnroll words per lane in flight: all word loads, then all
             // lI and weight loads, then the (fixed-order) accumulation; the
             // row-relative offsets, ring index and population lookup are 32-bit
@@ -207,11 +217,19 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adjoint(const __grid_constan
                 int idx[kAdjUnroll];
 #pragma unroll
                 for (int u = 0; u < kAdjUnroll; ++u) {
-                    const uint32_t tgt = word[u] & kTgtMask;
-                    const int pp = s_pop ? (int)s_pop[tgt] : pop_of_sorted(s_ps, (int32_t)tgt);
-                    idx[u] = pp * (kMaxPop * kWCodes) + (int)(word[u] >> 25);
-                    const uint32_t slot = (t32 + ((word[u] >> kTgtBits) & 63u)) & (kRing - 1);
-                    l[u] = o + 32u * (uint32_t)u < len ? __ldcg(&p.lring[slot * n32 + tgt]) : 0.f;
+                    if (PRE) {
+                        // (t + d) mod 64 rows of lring: offset + (t mod 64) n, wrapped
+                        idx[u] = (int)(word[u] >> kPreOffBits);
+                        uint32_t a = (word[u] & kPreOffMask) + (t32 & (kRing - 1)) * n32;
+                        a = min(a, a - (uint32_t)kRing * n32);
+                        l[u] = o + 32u * (uint32_t)u < len ? __ldcg(&p.lring[a]) : 0.f;
+                    } else {
+                        const uint32_t tgt = word[u] & kTgtMask;
+                        const int pp = s_pop ? (int)s_pop[tgt] : pop_of_sorted(s_ps, (int32_t)tgt);
+                        idx[u] = pp * (kMaxPop * kWCodes) + (int)(word[u] >> 25);
+                        const uint32_t slot = (t32 + ((word[u] >> kTgtBits) & 63u)) & (kRing - 1);
+                        l[u] = o + 32u * (uint32_t)u < len ? __ldcg(&p.lring[slot * n32 + tgt]) : 0.f;
+                    }
                 }
                 if (!spk) {
 #pragma unroll
@@ -264,6 +282,26 @@ __global__ void __launch_bounds__(kAdjThreads, 1) k_adjoint(const __grid_constan
         }
         if (!grid_barrier(p.barrier, p.abort_flag, p.status, p.timeout_ns, gen, &s_abort, false))
             break;
+    }
+}
+
+// One warp per row: the adjoint's pre-decoded entries from the packed words
+// (source population q of the row, target population p, delay d, code).
+__global__ void __launch_bounds__(256) k_adj_predecode(int32_t n, int32_t n_pop,
+                                                       const int32_t* pop_start,
+                                                       const unsigned long long* row_start,
+                                                       const uint32_t* words, uint32_t* pre) {
+    const int j = (int)((blockIdx.x * 256u + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    const uint32_t q = (uint32_t)pop_index(pop_start, n_pop, j);
+    const unsigned long long b = row_start[j], e = row_start[j + 1];
+    for (unsigned long long k = b + (unsigned long long)lane; k < e; k += 32ull) {
+        const uint32_t w = words[k];
+        const uint32_t tgt = w & kTgtMask;
+        const uint32_t pp = (uint32_t)pop_index(pop_start, n_pop, (int32_t)tgt);
+        const uint32_t widx = (pp * kMaxPop + q) * kWCodes + (w >> 25);
+        pre[k] = (widx << kPreOffBits) | (((w >> kTgtBits) & (kRing - 1)) * (uint32_t)n + tgt);
     }
 }
 
@@ -499,6 +537,15 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
                      : 0.0;
     GCK(cudaMemcpyAsync(g->out + kMaxPop * kMaxPop + 1, dnu, sizeof(dnu), cudaMemcpyHostToDevice, s));
     GCK(cudaMemcpyAsync(g->pop_start, net->pop_start, sizeof(int32_t) * (kMaxPop + 1), cudaMemcpyHostToDevice, s));
+    // pre-decoded rows for the gather, built once (the words never change);
+    // ring offsets 64 n must fit the entry's offset field
+    const bool use_pre = (long long)kRing * n < (long long)kPreOffMask;
+    if (use_pre && !g->pre) {
+        GCALL(galloc(&g->pre, (size_t)net->nnz + 4, "pre-decoded rows"));
+        k_adj_predecode<<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, s>>>(
+            n, net->n_pop, g->pop_start, net->d_row_start, net->d_words, g->pre);
+        GCK(cudaGetLastError());
+    }
 
     if (!g->blk) {
         // CTA row ranges with equal total row length, rows longest first
@@ -550,6 +597,7 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
     ap.timeout_ns = net->timeout_ns;
     ap.row_start = net->d_row_start;
     ap.words = net->d_words;
+    ap.pre = use_pre ? g->pre : nullptr;
     ap.wtab = net->d_wtab;
     ap.wbase = g->wbase;
     ap.tr_u = g->tr_u;
@@ -566,7 +614,9 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
     const size_t smem = 2 * sizeof(float) * kMaxPop * kMaxPop * kWCodes +
                         sizeof(unsigned long long) * ((size_t)ap.chunk + 1) + sizeof(float) * (size_t)ap.chunk +
                         (n <= kAdjPopTable ? (size_t)n : 0);
-    GCK(cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const void* adj_fn = use_pre ? reinterpret_cast<const void*>(&k_adjoint<true>)
+                                 : reinterpret_cast<const void*>(&k_adjoint<false>);
+    GCK(cudaFuncSetAttribute(adj_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
 
     StepParams sp;
     fill_step_params(net, &sp);
@@ -594,7 +644,7 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         void* args[] = {&ap};
-        GCK(cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(&k_adjoint), args));
+        GCK(cudaLaunchKernelExC(&cfg, adj_fn, args));
     }
     k_grad_reduce<<<1, 512, 0, s>>>(n, net->n_pop, g->pop_start, g->gA, g->gN, g->out + kMaxPop * kMaxPop + 1,
                                      g->out);
