@@ -221,6 +221,30 @@ __global__ void k_init_u(int n, uint32_t k0, uint32_t k1, float lo, float hi, fl
     u[i] = __fadd_rn(lo, __fmul_rn(span, unit));
 }
 
+// One CTA per partition: its offset is the sum of the clamped counts before it
+// (at most a few hundred partitions), then its first entries up to `limit`.
+__global__ void __launch_bounds__(256) k_pack_raster(const uint32_t* counts, int n_part,
+                                                     uint32_t cap_part, long long limit,
+                                                     const uint32_t* ras_step,
+                                                     const uint32_t* ras_id, uint32_t* step_out,
+                                                     uint32_t* id_out) {
+    __shared__ long long s_off;
+    const int c = blockIdx.x;
+    if (threadIdx.x == 0) {
+        long long o = 0;
+        for (int k = 0; k < c; ++k) o += min(counts[k], cap_part);
+        s_off = o;
+    }
+    __syncthreads();
+    const long long off = s_off;
+    const long long m = min((long long)min(counts[c], cap_part), limit - off);
+    const size_t base = (size_t)c * cap_part;
+    for (long long i = threadIdx.x; i < m; i += 256) {
+        step_out[off + i] = ras_step[base + (size_t)i];
+        id_out[off + i] = ras_id[base + (size_t)i];
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_build_count(const BuildParams& bp, uint32_t* rowlen, cudaStream_t s) {
@@ -265,6 +289,15 @@ cudaError_t launch_seg_from_rows(const unsigned long long* row_start, const uint
                                  int n, const int32_t* part_lo, int n_part, uint32_t* seg,
                                  cudaStream_t s) {
     k_seg_from_rows<<<n, kBuildThreads, 0, s>>>(row_start, words, part_lo, n_part, seg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_raster(const uint32_t* counts, int n_part, uint32_t cap_part,
+                               int64_t limit, const uint32_t* ras_step, const uint32_t* ras_id,
+                               uint32_t* step_out, uint32_t* id_out, cudaStream_t s) {
+    if (n_part <= 0 || limit <= 0) return cudaSuccess;
+    k_pack_raster<<<n_part, 256, 0, s>>>(counts, n_part, cap_part, (long long)limit, ras_step,
+                                         ras_id, step_out, id_out);
     return cudaGetLastError();
 }
 

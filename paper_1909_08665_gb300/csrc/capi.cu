@@ -187,7 +187,7 @@ void free_net(snn_net* net) {
     void* ptrs[] = {net->d_part_lo, net->d_row_start, net->d_seg, net->d_words, net->d_pre, net->d_wtab,
                     net->d_dtab, net->d_u, net->d_i, net->d_r, net->d_ring, net->d_msg, net->d_slots,
                     net->d_slot_base, net->d_slot_S,
-                    net->d_ras_step, net->d_ras_id, net->d_ras_n,
+                    net->d_ras_step, net->d_ras_id, net->d_ras_n, net->d_rs_step, net->d_rs_id,
                     net->d_counters, net->d_sync, net->d_pop_spikes, net->d_rt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -719,31 +719,39 @@ int snn_read_spikes(snn_net* net, uint32_t* steps_host, uint32_t* ids_host, int6
     CK(cudaStreamSynchronize(net->stream));
     std::vector<uint32_t> cnt(net->P);
     CK(cudaMemcpy(cnt.data(), net->d_ras_n, sizeof(uint32_t) * net->P, cudaMemcpyDeviceToHost));
-    int64_t got = 0;
-    bool lost = false, short_cap = false;
+    int64_t total = 0;
+    bool lost = false;
     for (int c = 0; c < net->P; ++c) {
-        uint32_t m = cnt[c];
-        if (m > net->ras_cap) {
-            lost = true;
-            m = net->ras_cap;
+        if (cnt[c] > net->ras_cap) lost = true;
+        total += std::min<uint32_t>(cnt[c], net->ras_cap);
+    }
+    // the first `cap` entries in partition order, packed on the device and
+    // copied back in one transfer per array
+    const int64_t got = std::min<int64_t>(total, cap);
+    if (got > 0 && (steps_host || ids_host)) {
+        if (net->rs_cap < (size_t)got) {
+            cudaFree(net->d_rs_step);
+            cudaFree(net->d_rs_id);
+            net->d_rs_step = net->d_rs_id = nullptr;
+            net->rs_cap = 0;
+            CALL(dalloc(&net->d_rs_step, (size_t)got, "raster staging"));
+            CALL(dalloc(&net->d_rs_id, (size_t)got, "raster staging"));
+            net->rs_cap = (size_t)got;
         }
-        const int64_t take = std::min<int64_t>(m, cap - got);
-        if (take < (int64_t)m) short_cap = true;
-        if (take > 0) {
-            if (steps_host)
-                CK(cudaMemcpy(steps_host + got, net->d_ras_step + (size_t)c * net->ras_cap,
-                              sizeof(uint32_t) * take, cudaMemcpyDeviceToHost));
-            if (ids_host)
-                CK(cudaMemcpy(ids_host + got, net->d_ras_id + (size_t)c * net->ras_cap,
-                              sizeof(uint32_t) * take, cudaMemcpyDeviceToHost));
-            got += take;
-        }
+        CK(launch_pack_raster(net->d_ras_n, net->P, net->ras_cap, got, net->d_ras_step,
+                              net->d_ras_id, net->d_rs_step, net->d_rs_id, net->stream));
+        if (steps_host)
+            CK(cudaMemcpyAsync(steps_host, net->d_rs_step, sizeof(uint32_t) * got,
+                               cudaMemcpyDeviceToHost, net->stream));
+        if (ids_host)
+            CK(cudaMemcpyAsync(ids_host, net->d_rs_id, sizeof(uint32_t) * got,
+                               cudaMemcpyDeviceToHost, net->stream));
     }
     CK(cudaMemsetAsync(net->d_ras_n, 0, sizeof(uint32_t) * net->P, net->stream));
     CK(cudaStreamSynchronize(net->stream));
     *n = got;
     if (lost) return fail(SNN_ERR_OVERFLOW, "spike raster capacity exceeded; spikes were lost");
-    if (short_cap) return fail(SNN_ERR_OVERFLOW, "cap smaller than the recorded spikes; the rest were dropped");
+    if (got < total) return fail(SNN_ERR_OVERFLOW, "cap smaller than the recorded spikes; the rest were dropped");
     return SNN_OK;
 }
 

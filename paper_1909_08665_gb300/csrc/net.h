@@ -56,6 +56,9 @@ struct snn_net {
     uint32_t* d_ras_step = nullptr;
     uint32_t* d_ras_id = nullptr;
     uint32_t* d_ras_n = nullptr;
+    uint32_t* d_rs_step = nullptr;          // raster read staging: every partition's entries packed
+    uint32_t* d_rs_id = nullptr;
+    size_t rs_cap = 0;                      // entries the staging arrays hold
     unsigned long long* d_counters = nullptr;
     uint32_t* d_sync = nullptr;   // [4] status, [5] abort
     unsigned long long* d_pop_spikes = nullptr;   // [8] spikes per population

@@ -242,6 +242,11 @@ cudaError_t launch_build_slots(const uint32_t* words, const uint32_t* seg, const
                                const int32_t* pop_start, int ncmax,
                                const unsigned long long* slot_base, const uint32_t* slot_S,
                                int2* slots, cudaStream_t s);
+// the raster entries of every partition (counts clamped to cap_part, then the
+// first `limit` entries in partition order) packed into step_out / id_out
+cudaError_t launch_pack_raster(const uint32_t* counts, int n_part, uint32_t cap_part,
+                               int64_t limit, const uint32_t* ras_step, const uint32_t* ras_id,
+                               uint32_t* step_out, uint32_t* id_out, cudaStream_t s);
 cudaError_t launch_init_state(int n, uint32_t key0, uint32_t key1, float lo, float hi,
                               float* u, cudaStream_t s);
 int step_kernel_variant(int npt, bool smem_ring);
