@@ -402,6 +402,21 @@ def run_batch(args):
     hbm_peak, peak_kind = load_peaks()
     achieved = BYTES_PER_EVENT * (events / (args.steps * launches_per_step)) / avg_launch_s / 1e9
     tilings = [b.info(k)["tiling"] for k in range(len(b))]
+    # end to end through the C ABI: every instance's raster read to the host
+    # after every bench step
+    barrier()
+    e0 = sum(b.counters(k)["events"] for k in range(len(b)))
+    t0 = time.perf_counter()
+    d2h = 0
+    h_steps = torch.empty(1 << 22, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    h_ids = torch.empty(1 << 22, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    for _ in range(args.steps):
+        b.step(chunk)
+        for k in range(len(b)):
+            d2h += 8 * b.read_spikes_into(k, h_steps, h_ids)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_events = sum(b.counters(k)["events"] for k in range(len(b))) - e0
     line = {
         "metric": METRIC, "value": events_all / (total_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -421,6 +436,9 @@ def run_batch(args):
         "events_per_time_step": events / (args.steps * chunk),
         "build_s": build_s, "clocks": clk.summary(),
         "gpu_launches": args.steps * launches_per_step,
+        "e2e": {"value": e2e_events * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": d2h // max(args.steps, 1),
+                "real_time_factor": e2e_s / bio_s},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
                      "kernel": "k_batch (persistent batched step kernel)"},

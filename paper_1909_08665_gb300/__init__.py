@@ -402,6 +402,7 @@ class MicrocircuitBatch:
         sd = np.ascontiguousarray(self.seeds, np.uint64)
         self._o = SnnOptions(0, int(inject_fault), int(raster_capacity), float(timeout_s))
         self.sizes = [int(sum(c["pop_sizes"])) for c in cfgs]
+        self._drained = {}                  # spikes read so far, per instance
         self.stream = _stream_handle(stream)
         h = C.c_void_p()
         _check(lib().snn_batch_create(arr, _ptr(sd, C.c_uint64), len(cfgs), C.byref(self._o),
@@ -427,16 +428,24 @@ class MicrocircuitBatch:
 
     def read_spikes(self, k: int, cap: int | None = None):
         """Drain instance k's spikes; returns (steps, ids) sorted by (step, id)."""
-        if cap is None:                     # spikes so far bound the undrained ones
-            cap = max(1, self.counters(k)["spikes"])
+        if cap is None:                     # spikes not read yet bound the undrained ones
+            cap = max(1, self.counters(k)["spikes"] - self._drained.get(k, 0))
         st = np.zeros(cap, np.uint32)
         ids = np.zeros(cap, np.uint32)
-        n = C.c_int64()
-        _check(lib().snn_batch_read_spikes(self._h, int(k), _ptr(st, C.c_uint32),
-                                           _ptr(ids, C.c_uint32), int(cap), C.byref(n)))
-        st, ids = st[:n.value], ids[:n.value]
+        n = self.read_spikes_into(k, st, ids)
+        st, ids = st[:n], ids[:n]
         order = np.lexsort((ids, st))
         return st[order].astype(np.int64), ids[order].astype(np.int64)
+
+    def read_spikes_into(self, k: int, steps_buf: np.ndarray, ids_buf: np.ndarray) -> int:
+        """Drain instance k's spikes into caller-provided uint32 host buffers
+        (ids relative to the instance, in recording order, not sorted)."""
+        n = C.c_int64()
+        _check(lib().snn_batch_read_spikes(self._h, int(k), _ptr(steps_buf, C.c_uint32),
+                                           _ptr(ids_buf, C.c_uint32), int(steps_buf.size),
+                                           C.byref(n)))
+        self._drained[k] = self._drained.get(k, 0) + n.value
+        return n.value
 
     def state(self, k: int):
         n = self.sizes[k]

@@ -570,6 +570,7 @@ struct snn_batch {
     bool graph_ok = false;
     long long step = 0;
     std::vector<std::vector<uint32_t>> host_steps, host_ids;   // drained raster per instance
+    std::vector<uint16_t> inst_of;  // instance of every global neuron id (built on the first drain)
     std::vector<float2> u0_range;        // default initial potentials per instance
     float trial_us = 0.f;                // per-step time of the chosen assignment
 };
@@ -782,9 +783,21 @@ int drain_raster(snn_batch* b) {
         BCK(cudaMemcpy(id.data(), b->d_ras_id, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost));
     }
     BCK(cudaMemset(b->d_ras_n, 0, sizeof(uint32_t)));
+    if (b->inst_of.empty()) {
+        b->inst_of.resize((size_t)b->ntot);
+        for (int k = 0; k < b->n_inst; ++k)
+            std::fill(b->inst_of.begin() + b->goff[k], b->inst_of.begin() + b->goff[k + 1],
+                      (uint16_t)k);
+    }
+    // per-instance counts first, so that each instance's buffers grow once
+    std::vector<uint32_t> cnt((size_t)b->n_inst, 0u);
+    for (uint32_t r = 0; r < m; ++r) ++cnt[b->inst_of[id[r]]];
+    for (int k = 0; k < b->n_inst; ++k) {
+        b->host_steps[k].reserve(b->host_steps[k].size() + cnt[k]);
+        b->host_ids[k].reserve(b->host_ids[k].size() + cnt[k]);
+    }
     for (uint32_t r = 0; r < m; ++r) {
-        const int k = (int)(std::upper_bound(b->goff.begin(), b->goff.end(), (int32_t)id[r]) -
-                            b->goff.begin()) - 1;
+        const int k = b->inst_of[id[r]];
         b->host_steps[k].push_back(st[r]);
         b->host_ids[k].push_back(id[r] - (uint32_t)b->goff[k]);
     }
