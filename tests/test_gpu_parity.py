@@ -304,6 +304,44 @@ def test_barrier_timeout_reports_error_and_context_survives(cfg01):
     ok.sync()
 
 
+def test_raster_reads_in_parts_and_with_a_short_cap(cfg01):
+    """snn_read_spikes packs every partition's entries on the device: a read
+    with a short cap returns the first entries in partition order and reports
+    the rest as dropped, and reads between steps add up to one read of the
+    whole run.  Within one step of one partition the recording order is not
+    fixed (warps append concurrently), so the prefix is compared by the steps
+    it covers and by membership."""
+    a, b = gpu_net(cfg01), gpu_net(cfg01)
+    a.step(300)
+    b.step(300)
+    full_st = np.zeros(1 << 20, np.uint32)
+    full_id = np.zeros(1 << 20, np.uint32)
+    n = a.read_spikes_into(full_st, full_id)
+    assert n > 100
+    st = np.zeros(n // 2, np.uint32)
+    ids = np.zeros(n // 2, np.uint32)
+    with pytest.raises(pkg.SnnError) as e:
+        b.read_spikes_into(st, ids)
+    assert e.value.code == pkg.SNN_ERR_OVERFLOW
+    np.testing.assert_array_equal(np.sort(st), np.sort(full_st[:n // 2]))
+    whole_a = set(zip(full_st[:n].tolist(), full_id[:n].tolist()))
+    assert set(zip(st.tolist(), ids.tolist())) <= whole_a
+    c, d = gpu_net(cfg01), gpu_net(cfg01)
+    parts = []
+    for _ in range(3):
+        c.step(100)
+        parts.append(c.read_spikes())
+    d.step(300)
+    whole = d.read_spikes()
+    pst = np.concatenate([q[0] for q in parts])
+    pid = np.concatenate([q[1] for q in parts])
+    order = np.lexsort((pid, pst))
+    np.testing.assert_array_equal(pst[order], whole[0])
+    np.testing.assert_array_equal(pid[order], whole[1])
+    for x in (a, b, c, d):
+        x.close()
+
+
 def test_raster_overflow_is_reported(cfg01):
     net = gpu_net(cfg01, raster_capacity=1)
     net.step(400)
