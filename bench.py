@@ -53,12 +53,12 @@ UNIT = "synaptic events/s"
 STEPS_PER_BENCH_STEP = 10000          # 1 s of biological time at dt = 0.1 ms
 BYTES_PER_EVENT = 4                   # one packed synaptic word read per event
 # DRAM bytes (read + write) per time step of k_step on the full microcircuit,
-# from one ncu capture of this kernel (profiles/k_step_full_microcircuit_dram.md);
-# None for any other workload, and to be re-measured whenever k_step changes
+# from one ncu capture of this kernel (dram__bytes_read.sum + write.sum of one
+# 2000-step launch, divided by its steps); None for any other workload, and to
+# be re-measured whenever k_step changes
 K_STEP_DRAM_BYTES_PER_STEP_FULL = (14161993728 + 4584960) / 2000.0
 # k_deliver_words, 20,000-spike lists at scale 1: ncu dram__bytes_read + write
-# of three launches (profiles/k_deliver_words_20000_spikes_dram.md) over their
-# mean synaptic events
+# of three launches over their mean synaptic events
 K_DELIVER_WORDS_DRAM_BYTES_PER_EVENT = (349.75e6 + 348.93e6 + 349.31e6) / 3.0 / 77.78e6
 
 
@@ -332,9 +332,9 @@ def run_ours(args):
                      "frac": achieved / hbm_peak,
                      "traffic": (K_STEP_DRAM_BYTES_PER_STEP_FULL * chunk
                                  if args.scale == 1.0 else None),
-                     "traffic_source": ("ncu dram__bytes of one 2000-step launch, scaled by "
-                                        "steps per launch (profiles/"
-                                        "k_step_full_microcircuit_dram.md)"
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                        "of one 2000-step k_step launch on the full "
+                                        "microcircuit, scaled by steps per launch"
                                         if args.scale == 1.0 else None),
                      "peak_kind": peak_kind, "kernel": "k_step (persistent step kernel)"},
     }

@@ -258,9 +258,13 @@ int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int6
  * device array of 64 + 2 * SNN_NOALLOC_MAX_NEURONS 32-bit words (about 1 MiB)
  * that every GPU loading this library holds until the process exits.
  * Networks above SNN_NOALLOC_MAX_NEURONS neurons are rejected with
- * SNN_ERR_INVALID.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the one array and
+ * SNN_ERR_INVALID.  The first call on a device does that device's set-up,
+ * with that device current: it looks up the array's device address
+ * (cudaGetSymbolAddress) and queries the device's architecture, SM count and
+ * the kernel's occupancy, and keeps them for the life of the process; make
+ * that first call before any stream capture.  Do not use this entry point on
+ * a device after cudaDeviceReset() of that device in the same process: the
+ * kept address may no longer be the array's.  Every call shares the one array and
  * clears the words that must start at zero, so calls whose kernels overlap
  * on the GPU (on different streams, or from several threads) race and give
  * wrong results: serialise them.

@@ -202,9 +202,34 @@ __global__ void __launch_bounds__(kNaThreads, 1) k_step_noalloc(const __grid_con
     }
 }
 
+// set-up of each device, done once by its first call: the scratch array's
+// device address, the architecture check, the SM count and the co-resident
+// CTAs per SM of the kernel (so that a call only fills parameters, clears the
+// scratch header and launches)
+struct NaDevice {
+    uint32_t* scratch;
+    cudaError_t err;
+    const char* what;                   // the set-up call that failed
+    bool arch_ok;
+    int sms, per_sm;
+};
 std::once_flag g_setup_once[kNaMaxDevices];
-uint32_t* g_scratch_ptr[kNaMaxDevices];
-cudaError_t g_setup_err[kNaMaxDevices];
+NaDevice g_dev[kNaMaxDevices];
+
+void setup_device(int dev) {
+    NaDevice& d = g_dev[dev];
+    d.what = "cudaGetSymbolAddress(g_noalloc_scratch)";
+    d.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&d.scratch), g_noalloc_scratch);
+    if (d.err != cudaSuccess) return;
+    cudaDeviceProp prop;
+    d.what = "cudaGetDeviceProperties";
+    d.err = cudaGetDeviceProperties(&prop, dev);
+    if (d.err != cudaSuccess) return;
+    d.arch_ok = prop.major == 10 && prop.minor == 3;
+    d.sms = prop.multiProcessorCount;
+    d.what = "occupancy query";
+    d.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.per_sm, k_step_noalloc, kNaThreads, 0);
+}
 
 }  // namespace
 }  // namespace snn
@@ -241,25 +266,14 @@ extern "C" int snn_step_noalloc(const snn_config* cfg, uint64_t seed, const snn_
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_cuda_error(e, "cudaGetDevice");
     if (dev < 0 || dev >= kNaMaxDevices) return set_error(SNN_ERR_UNSUPPORTED, "device index too large");
-    std::call_once(g_setup_once[dev], [dev] {
-        g_setup_err[dev] = cudaGetSymbolAddress(reinterpret_cast<void**>(&g_scratch_ptr[dev]),
-                                                g_noalloc_scratch);
-    });
-    if (g_setup_err[dev] != cudaSuccess)
-        return set_cuda_error(g_setup_err[dev], "cudaGetSymbolAddress(g_noalloc_scratch)");
-
-    cudaDeviceProp prop;
-    e = cudaGetDeviceProperties(&prop, dev);
-    if (e != cudaSuccess) return set_cuda_error(e, "cudaGetDeviceProperties");
-    if (prop.major != 10 || prop.minor != 3)
+    std::call_once(g_setup_once[dev], setup_device, dev);
+    const NaDevice& d = g_dev[dev];
+    if (d.err != cudaSuccess) return set_cuda_error(d.err, d.what);
+    if (!d.arch_ok)
         return set_error(SNN_ERR_UNSUPPORTED, "this library is built for sm_103 (GB300) GPUs only");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_noalloc, kNaThreads, 0);
-    if (e != cudaSuccess) return set_cuda_error(e, "occupancy query");
-    if (per_sm < 1) return set_error(SNN_ERR_UNSUPPORTED, "step kernel does not fit an SM");
+    if (d.per_sm < 1) return set_error(SNN_ERR_UNSUPPORTED, "step kernel does not fit an SM");
     // one CTA per SM at most, about 256 neurons per CTA for small networks
-    const int P = (int)std::min<long long>(prop.multiProcessorCount,
-                                           std::max<long long>(1, (n + 255) / 256));
+    const int P = (int)std::min<long long>(d.sms, std::max<long long>(1, (n + 255) / 256));
 
     p.n = (int32_t)n;
     p.n_pop = cfg->n_pop;
@@ -287,7 +301,7 @@ extern "C" int snn_step_noalloc(const snn_config* cfg, uint64_t seed, const snn_
     p.ras_cap = (uint32_t)std::min<int64_t>(std::max<int64_t>(io->ras_cap, 0), 0x7fffffff);
     p.counters = io->counters;
     p.status = io->status;
-    p.scratch = g_scratch_ptr[dev];
+    p.scratch = d.scratch;
 
     // the shared scratch keeps the previous call's contents: clear the
     // barrier, status and list-counter words that must start at zero

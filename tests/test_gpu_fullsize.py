@@ -3,7 +3,7 @@ the launch configuration the benchmark times, plus the statistical comparison
 the paper uses between simulators (Sec. 4.2).
 
 The oracle builds the full network itself (all host cores); spike rasters and
-fp32 state are compared bit for bit over 100 steps, and single rows of the
+fp32 state are compared bit for bit over 1000 steps, and single rows of the
 network are compared against the oracle's stand-alone row generator.
 """
 import os
@@ -40,14 +40,14 @@ def test_full_size_sampled_rows(full):
         np.testing.assert_array_equal(wd[rp[j]:rp[j + 1]], pkg.encode_words(tg, dl, wc))
 
 
-def test_full_size_raster_bit_exact_100_steps(full):
+def test_full_size_raster_bit_exact_1000_steps(full):
     cfg, _ = full
     net = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
     info = net.info()
     assert info["n_part"] >= 100 and info["ring_in_shared"] == 1    # the benchmark's launch shape
     onet = oracle.Network(cfg, n_threads=os.cpu_count())
     sim = oracle.Simulation(onet)
-    steps = 100
+    steps = 1000
     net.step(steps)
     net.sync()
     sim.run(steps)
@@ -65,16 +65,25 @@ def test_full_size_raster_bit_exact_100_steps(full):
     assert net.counters()["events"] == sim.counters()["events"]
 
 
-def test_full_size_delivery_both_tilings(full):
+@pytest.mark.parametrize("n_spikes", [4000, 20000])
+def test_full_size_delivery_every_tiling(full, n_spikes):
+    """Every tiling of the stand-alone delivery at the list sizes the
+    delivery benchmark times (20,000 spikes: 7.8e7 synaptic events, the
+    partition-word tiling's multi-round path), into a ring that already holds
+    an earlier list's input."""
     cfg, net = full
     onet = oracle.Network(cfg, n_threads=os.cpu_count())
+    first = workload.random_spike_list(net.n, 500, seed=5).astype(np.int32)
+    d_first = torch.from_numpy(first).cuda()
     for tiling in (0, 1, 2, 3, 4):
         fresh = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
-        spikes = workload.random_spike_list(fresh.n, 4000, seed=11 + tiling)
-        d = torch.from_numpy(spikes.astype(np.int32)).cuda()
+        spikes = workload.random_spike_list(fresh.n, n_spikes, seed=11 + tiling).astype(np.int32)
+        d = torch.from_numpy(spikes).cuda()
+        fresh.deliver(d_first.data_ptr(), first.size, 13, tiling)
         fresh.deliver(d.data_ptr(), spikes.size, 777, tiling)
         fresh.sync()
-        ref = onet.deliver(spikes.astype(np.int32), 777)
+        ref = onet.deliver(first, 13)
+        ref = onet.deliver(spikes, 777, ring=ref)
         np.testing.assert_array_equal(fresh.ring(), ref.astype(np.int32))
         fresh.close()
 
@@ -120,13 +129,15 @@ def test_statistics_agree_across_seeds():
 def test_scale4_short_run_bit_exact():
     """The 4x network (308,676 neurons, ~1.2e9 synapses, same in-degrees):
     ring buffers in global memory and 4 neurons per thread, the launch shape
-    the scale-up benchmark times; 30 steps bit for bit against the oracle."""
+    the scale-up benchmark times; 300 steps bit for bit against the oracle,
+    and stand-alone delivery of 4,000 and 20,000 spikes into ring slices in
+    global memory on every tiling that supports them."""
     cfg = workload.microcircuit(4.0)
     net = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
     info = net.info()
     assert info["ring_in_shared"] == 0 and info["neurons_per_thread"] == 4
     assert abs(info["n_synapses"] / 1.2e9 - 1.0) < 0.01
-    steps = 30
+    steps = 300
     net.step(steps)
     net.sync()
     g = net.read_spikes()
@@ -147,12 +158,14 @@ def test_scale4_short_run_bit_exact():
     assert c["events"] == sim.counters()["events"]
     # stand-alone delivery into ring slices in global memory, with every
     # partition inside at most two populations
-    spikes = workload.random_spike_list(info["n_neurons"], 4000, seed=44).astype(np.int32)
-    ref = onet.deliver(spikes, 4321).astype(np.int32)
-    d = torch.from_numpy(spikes).cuda()
-    for tiling in (1, 3):
-        fresh = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
-        fresh.deliver(d.data_ptr(), spikes.size, 4321, tiling)
-        fresh.sync()
-        np.testing.assert_array_equal(fresh.ring(), ref)
-        fresh.close()
+    for m in (4000, 20000):
+        spikes = workload.random_spike_list(info["n_neurons"], m, seed=44).astype(np.int32)
+        ref = onet.deliver(spikes, 4321).astype(np.int32)
+        d = torch.from_numpy(spikes).cuda()
+        for tiling in (0, 1, 2, 3):
+            fresh = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
+            fresh.deliver(d.data_ptr(), spikes.size, 4321, tiling)
+            fresh.sync()
+            np.testing.assert_array_equal(fresh.ring(), ref)
+            fresh.close()
+        del ref

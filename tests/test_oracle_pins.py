@@ -457,3 +457,55 @@ def test_statistics_on_known_trains():
     cfg = workload.microcircuit(0.1)
     r = oracle.population_rates(cfg, np.zeros(2068, np.int64), np.arange(2068), 0, 10000)
     assert abs(r[0] - 1.0) < 1e-12 and r[1:].sum() == 0
+
+
+# --------------------------------------------------------------------------
+# stand-alone delivery (step 6 alone) pinned two ways: against the ring
+# change of one full oracle step with a forced spike list, and against arrival
+# sums written directly from the synapse list of a hand-set network
+# --------------------------------------------------------------------------
+def test_deliver_equals_ring_change_of_one_step(net01):
+    """Neurons set far above threshold spike in the next step and no other
+    does (the rest start at rest with no current, so one step of input cannot
+    lift them to threshold); that step leaves in the ring exactly the rows of
+    the forced spikes, which is what the stand-alone delivery must add."""
+    cfg, net, (rp, _, _, _) = net01
+    n = net.n
+    spikes = workload.random_spike_list(n, 300, seed=17).astype(np.int32)
+    t = 1234
+    sim = oracle.Simulation(net)
+    u = np.zeros(n, np.float32)
+    u[spikes] = 25.0
+    sim.set_state(u, np.zeros(n, np.float32), np.zeros(n, np.int32),
+                  np.zeros((64, n), np.int64), t)
+    sim.run(1)
+    st, ids = sim.raster()
+    assert np.all(st == t)
+    np.testing.assert_array_equal(ids, np.sort(spikes))
+    ring = sim.state()[3]
+    ref = net.deliver(spikes, t)
+    np.testing.assert_array_equal(ring, ref)
+    assert sim.counters()["events"] == int(np.diff(rp)[spikes].sum())
+    # duplicates in a list add twice; the result is linear in the list
+    twice = net.deliver(np.r_[spikes, spikes], t)
+    np.testing.assert_array_equal(twice, 2 * ref)
+    assert cfg["ring_depth"] == 64
+
+
+def test_deliver_brute_force_tiny_network():
+    n = 6
+    weights_q = [round(87.8 * 256 * 12), round(-351.2 * 256 * 3), round(87.8 * 256 * 20)]
+    synapses = [(0, 1, 0, 3), (0, 2, 2, 15), (1, 3, 2, 1), (2, 3, 1, 5), (3, 4, 0, 40),
+                (4, 5, 2, 63), (5, 0, 1, 9), (3, 5, 2, 2), (1, 0, 1, 30), (0, 5, 1, 63)]
+    cfg = tiny_config(n)
+    desc = custom_network(n, synapses, weights_q)
+    net = oracle.Network(cfg, custom=desc)
+    spikes = [0, 3, 1, 0, 5, 4, 4]
+    for t in (0, 7, 61, 1000003):
+        got = net.deliver(np.asarray(spikes, np.int32), t)
+        want = np.zeros((64, n), np.int64)
+        for j in spikes:                       # every synapse of every listed source
+            for (s, tg, wi, d) in synapses:
+                if s == j:
+                    want[(t + d) % 64, tg] += weights_q[wi]
+        np.testing.assert_array_equal(got, want)

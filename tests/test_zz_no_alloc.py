@@ -82,6 +82,77 @@ def test_noalloc_matches_step_on_two_calls():
         t0 += n
 
 
+def _noalloc_buffers(cfg, rp, words, wtab, u0, cap):
+    """Every device buffer of snn_step_noalloc, owned by the test (torch)."""
+    n = int(sum(cfg["pop_sizes"]))
+    bufs = {
+        "rp": _dev(rp, np.int64), "words": _dev(words, np.int32),
+        "wtab": _dev(np.asarray(wtab, np.int32).reshape(-1), np.int32),
+        "u": _dev(np.asarray(u0, np.float32).copy(), np.float32),
+        "i": torch.zeros(n, dtype=torch.float32, device="cuda"),
+        "r": torch.zeros(n, dtype=torch.int32, device="cuda"),
+        "ring": torch.zeros(64 * n, dtype=torch.int32, device="cuda"),
+        "rs": torch.zeros(cap, dtype=torch.int32, device="cuda"),
+        "ri": torch.zeros(cap, dtype=torch.int32, device="cuda"),
+        "rn": torch.zeros(1, dtype=torch.int32, device="cuda"),
+        "cnt": torch.zeros(2, dtype=torch.int64, device="cuda"),
+        "status": torch.zeros(1, dtype=torch.int32, device="cuda"),
+    }
+    io = pkg.SnnNoallocIO(
+        row_ptr=bufs["rp"].data_ptr(), words=bufs["words"].data_ptr(),
+        wtab=bufs["wtab"].data_ptr(), u=bufs["u"].data_ptr(), i_syn=bufs["i"].data_ptr(),
+        refr=bufs["r"].data_ptr(), ring=bufs["ring"].data_ptr(), ras_step=bufs["rs"].data_ptr(),
+        ras_id=bufs["ri"].data_ptr(), ras_n=bufs["rn"].data_ptr(), ras_cap=cap,
+        counters=bufs["cnt"].data_ptr(), status=bufs["status"].data_ptr())
+    return bufs, io
+
+
+@pytest.mark.parametrize("scale,mode", [(0.1, "dc"), (1.6, "poisson")])
+def test_noalloc_matches_oracle(scale, mode):
+    """Against the CPU oracle directly, on two calls in a row: the DC-input
+    variant at 10 % scale, and a network of 123,470 neurons, just under the
+    entry point's limit, whose spike lists fill most of the static scratch."""
+    import os
+
+    import oracle
+    cfg = workload.microcircuit(scale, input_mode=mode)
+    n = int(sum(cfg["pop_sizes"]))
+    assert n <= pkg.NOALLOC_MAX_NEURONS
+    onet = oracle.Network(cfg, n_threads=os.cpu_count())
+    rp, tg, dl, wc = onet.export()
+    words = pkg.encode_words(tg, dl, wc)
+    u0 = workload.random_membrane(cfg, seed=77)
+    stream = torch.cuda.current_stream()
+    bufs, io = _noalloc_buffers(cfg, rp.astype(np.uint64), words, oracle.tables(cfg)["wtab"],
+                                u0, 1 << 22)
+    sim = oracle.Simulation(onet, u0=u0)
+    t0 = 0
+    for steps in (120, 180):
+        pkg.step_noalloc(cfg, cfg["seed"], io, t0, steps, stream)
+        torch.cuda.synchronize()
+        sim.run(steps)
+        assert int(bufs["status"].item()) == 0
+        nrec = int(bufs["rn"].item())
+        st = bufs["rs"][:nrec].cpu().numpy().astype(np.int64)
+        ids = bufs["ri"][:nrec].cpu().numpy().astype(np.int64)
+        order = np.lexsort((ids, st))
+        o_st, o_id = sim.raster()
+        assert o_st.size > 50
+        np.testing.assert_array_equal(st[order], o_st)
+        np.testing.assert_array_equal(ids[order], o_id)
+        bufs["rn"].zero_()
+        o_u, o_i, o_r, o_ring = sim.state()
+        np.testing.assert_array_equal(bufs["u"].cpu().numpy().view(np.uint32), o_u.view(np.uint32))
+        np.testing.assert_array_equal(bufs["i"].cpu().numpy().view(np.uint32), o_i.view(np.uint32))
+        np.testing.assert_array_equal(bufs["r"].cpu().numpy(), o_r)
+        np.testing.assert_array_equal(bufs["ring"].cpu().numpy().reshape(64, n),
+                                      o_ring.astype(np.int32))
+        oc = sim.counters()
+        assert int(bufs["cnt"][0].item()) == oc["spikes"]
+        assert int(bufs["cnt"][1].item()) == oc["events"]
+        t0 += steps
+
+
 def test_noalloc_rejects_networks_above_its_limit():
     cfg = workload.microcircuit(2.0)           # 154,338 neurons
     assert sum(cfg["pop_sizes"]) > pkg.NOALLOC_MAX_NEURONS

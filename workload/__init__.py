@@ -242,6 +242,22 @@ def random_membrane(cfg: dict, seed: int, lo: float = 0.0, hi: float | None = No
     return rng.uniform(lo, hi, n_neurons(cfg)).astype(np.float32)
 
 
+def transient_membrane(cfg: dict, seed: int, n_above: int, lo_above: float = 16.0,
+                       hi_above: float = 30.0):
+    """Seeded fp32 membrane potentials of an unrelaxed start: ``n_above``
+    distinct neurons drawn uniformly in [lo_above, hi_above) mV, far enough
+    above the 15 mV threshold to stay above it after one step of leak, the
+    rest uniform in [0, theta).  The paper starts from relaxed values because
+    unrelaxed ones fire more than 4000 neurons in the first step (Sec. 2.3);
+    this input reproduces that transient on purpose."""
+    rng = np.random.default_rng(seed)
+    n = n_neurons(cfg)
+    u = rng.uniform(0.0, cfg["theta"], n)
+    above = rng.choice(n, min(int(n_above), n), replace=False)
+    u[above] = rng.uniform(lo_above, hi_above, above.size)
+    return u.astype(np.float32)
+
+
 def random_spike_list(n_neurons_: int, n_spikes: int, seed: int):
     """Distinct random source neuron ids, as a delivery-test spike list."""
     rng = np.random.default_rng(seed)
