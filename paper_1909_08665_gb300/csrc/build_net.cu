@@ -178,38 +178,6 @@ __global__ void k_max_segment(const uint32_t* seg, int n, int n_part, uint32_t* 
     }
 }
 
-// Partition slots: slot (j, c) is a run of 8-byte entries; entry 0 holds the
-// number of row j's synapses onto partition c, entries 1.. hold those
-// synapses ready for accumulation: the fixed-point weight
-// wtab[pop(i)][pop(j)][code] and the ring offset delay * ncmax + (i - part_lo[c]).
-// The step kernel adds the weight at ((t mod 64) * ncmax + offset) mod (64 ncmax).
-// Slots are partition-major: slot (j, c) starts at slot_base[c] + j * S_c,
-// where S_c (a power of two, >= 32) exceeds partition c's longest segment, so
-// one partition's slots form one contiguous region.  One warp per (j, c).
-__global__ void __launch_bounds__(kBuildThreads)
-k_build_slots(const uint32_t* words, const uint32_t* seg, const int32_t* part_lo,
-              const int32_t* wtab, int n, int n_part, int n_pop, SlotPops pops, int ncmax,
-              const unsigned long long* slot_base, const uint32_t* slot_S, int2* slots) {
-    const size_t warp_id = ((size_t)blockIdx.x * kBuildThreads + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp_id >= (size_t)n * n_part) return;
-    const size_t j = warp_id / n_part;
-    const int c = (int)(warp_id % n_part);
-    const int q = pop_index(pops.pop_start, n_pop, (int32_t)j);
-    const uint32_t* r = seg + j * (n_part + 1) + c;
-    const uint32_t b = r[0], e = r[1];
-    const int32_t lo = part_lo[c];
-    int2* out = slots + slot_base[c] + j * (size_t)slot_S[c];
-    if (lane == 0) out[0] = make_int2((int)(e - b), 0);
-    for (uint32_t k = b + lane; k < e; k += 32) {
-        const uint32_t w = words[k];
-        const int32_t tgt = (int32_t)(w & kTgtMask);
-        const int p = pop_index(pops.pop_start, n_pop, tgt);
-        const int32_t wq = wtab[(p * kMaxPop + q) * kWCodes + (int)(w >> 25)];
-        const int32_t off = (int32_t)((w >> kTgtBits) & 63u) * ncmax + (tgt - lo);
-        out[1 + (k - b)] = make_int2(wq, off);
-    }
-}
 
 // default initial potential: uniform on [lo, hi) from 24 random bits, fp32
 __global__ void k_init_u(int n, uint32_t k0, uint32_t k1, float lo, float hi, float* u) {
@@ -267,21 +235,6 @@ cudaError_t launch_build_fill(const BuildParams& bp, const unsigned long long* r
 cudaError_t launch_max_segment(const uint32_t* seg, int n, int n_part, uint32_t* out,
                                cudaStream_t s) {
     k_max_segment<<<n_part, kBuildThreads, 0, s>>>(seg, n, n_part, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_build_slots(const uint32_t* words, const uint32_t* seg, const int32_t* part_lo,
-                               const int32_t* wtab, int n, int n_part, int n_pop,
-                               const int32_t* pop_start, int ncmax,
-                               const unsigned long long* slot_base, const uint32_t* slot_S,
-                               int2* slots, cudaStream_t s) {
-    SlotPops pops;
-    for (int p = 0; p <= kMaxPop; ++p) pops.pop_start[p] = pop_start[p];
-    const size_t warps = (size_t)n * n_part;
-    const size_t blocks = (warps * 32 + kBuildThreads - 1) / kBuildThreads;
-    k_build_slots<<<(unsigned)blocks, kBuildThreads, 0, s>>>(words, seg, part_lo, wtab, n, n_part,
-                                                            n_pop, pops, ncmax, slot_base, slot_S,
-                                                            slots);
     return cudaGetLastError();
 }
 

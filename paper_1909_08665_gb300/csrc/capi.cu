@@ -185,8 +185,7 @@ int make_tables(snn_net* net) {
 void free_net(snn_net* net) {
     if (!net) return;
     void* ptrs[] = {net->d_part_lo, net->d_row_start, net->d_seg, net->d_words, net->d_pre, net->d_wtab,
-                    net->d_dtab, net->d_u, net->d_i, net->d_r, net->d_ring, net->d_msg, net->d_slots,
-                    net->d_slot_base, net->d_slot_S,
+                    net->d_dtab, net->d_u, net->d_i, net->d_r, net->d_ring, net->d_msg,
                     net->d_ras_step, net->d_ras_id, net->d_ras_n, net->d_rs_step, net->d_rs_id,
                     net->d_counters, net->d_sync, net->d_pop_spikes, net->d_rt};
     for (void* p : ptrs)
@@ -238,11 +237,14 @@ int plan(snn_net* net, const snn_options* opt) {
     else if (npt <= 8) npt = 8;
     else return fail(SNN_ERR_INVALID, "too many neurons per partition (raise n_part)");
     net->npt = npt;
+    if ((long long)kRing * ncmax >= (long long)kPreOffMask)
+        return fail(SNN_ERR_INVALID, "partition too large for the 19-bit ring offsets");
+    net->w_span = partition_pop_span(net->part_lo.data(), P, net->pop_start, net->n_pop);
     int smem_max = 0;
     CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t with_ring = step_shared_bytes(ncmax, P, true);
+    const size_t with_ring = step_shared_bytes(ncmax, P, net->w_span, true);
     net->smem_ring = with_ring <= (size_t)smem_max;
-    net->smem = step_shared_bytes(ncmax, P, net->smem_ring);
+    net->smem = step_shared_bytes(ncmax, P, net->w_span, net->smem_ring);
     CK(step_kernel_configure(npt, net->smem_ring, net->smem));
     int per_sm = 0;
     CK(step_max_blocks(npt, net->smem_ring, net->smem, &per_sm));
@@ -316,13 +318,13 @@ int common_setup(const snn_config* cfg, uint64_t seed, const snn_options* opt, v
     return SNN_OK;
 }
 
-// weight table upload and the partition slots of the step kernel
+// weight table upload and the pre-decoded rows the step kernel reads: entry
+// k of row j is (weight-table index << 19) | (delay * ncmax + target - its
+// partition's start), the same layout as the packed words
 int finish_network(snn_net* net) {
     cudaStream_t s = net->stream;
     CALL(dalloc(&net->d_wtab, kMaxPop * kMaxPop * kWCodes, "wtab"));
     CK(cudaMemcpyAsync(net->d_wtab, net->wtab, sizeof(net->wtab), cudaMemcpyHostToDevice, s));
-    // per partition c: S_c = power of two >= its longest segment + 1 (entry 0
-    // is the count), at least 32; partition c's slots start at base_c
     const int P = net->P;
     uint32_t* d_max = nullptr;
     CALL(dalloc(&d_max, P, "segment maxima"));
@@ -333,29 +335,18 @@ int finish_network(snn_net* net) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_max);
     if (e != cudaSuccess) return cuda_fail(e, "segment maxima");
-    std::vector<uint32_t> S(P);
-    std::vector<unsigned long long> base(P);
-    uint64_t total = 0;
-    int smax = 32;
-    for (int c = 0; c < P; ++c) {
-        uint32_t se = 32;
-        while (se < lmax[c] + 1) se *= 2;
-        S[c] = se;
-        base[c] = total;
-        total += (uint64_t)net->n * se;
-        smax = std::max(smax, (int)se);
-    }
-    net->slot_entries = smax;
-    net->slot_total = total;
-    CALL(dalloc(&net->d_slot_base, P, "slot offsets"));
-    CALL(dalloc(&net->d_slot_S, P, "slot strides"));
-    CK(cudaMemcpyAsync(net->d_slot_base, base.data(), sizeof(unsigned long long) * P,
-                       cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(net->d_slot_S, S.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, s));
-    CALL(dalloc(&net->d_slots, (size_t)total + 32, "partition slots"));
-    CK(launch_build_slots(net->d_words, net->d_seg, net->d_part_lo, net->d_wtab, net->n, P,
-                          net->n_pop, net->pop_start, net->ncmax, net->d_slot_base, net->d_slot_S,
-                          net->d_slots, s));
+    net->run_max = (int32_t)*std::max_element(lmax.begin(), lmax.end());
+    CALL(dalloc(&net->d_pre, (size_t)net->nnz + 4, "pre-decoded rows"));
+    DeliverParams dp;
+    std::memset(&dp, 0, sizeof(dp));
+    dp.n = net->n;
+    dp.n_pop = net->n_pop;
+    dp.n_part = P;
+    dp.ncmax = net->ncmax;
+    for (int p = 0; p <= kMaxPop; ++p) dp.pop_start[p] = net->pop_start[p];
+    dp.part_lo = net->d_part_lo;
+    dp.words = net->d_words;
+    CK(launch_predecode(dp, net->d_row_start, net->d_pre, s));
     CK(cudaStreamSynchronize(s));
     return SNN_OK;
 }
@@ -547,9 +538,8 @@ void fill_step_params(const snn_net* net, StepParams* out) {
     for (int p = 0; p < kMaxPop; ++p)
         for (int m = 0; m < kPoisTable; ++m)   // T >= 1 (validation bounds lambda)
             sp.pois_m1[p][m] = (uint32_t)(net->pois[p][m] - 1u);
-    sp.slots = net->d_slots;
-    sp.slot_base = net->d_slot_base;
-    sp.slot_S = net->d_slot_S;
+    sp.pre = net->d_pre;
+    sp.w_span = net->w_span;
     sp.part_lo = net->d_part_lo;
     sp.seg = net->d_seg;
     sp.words = net->d_words;
@@ -609,11 +599,21 @@ void net_base_weights(const snn_net* net, float* wb) {
 int net_upload_weights(snn_net* net) {
     cudaStream_t s = net->stream;
     CK(cudaMemcpyAsync(net->d_wtab, net->wtab, sizeof(net->wtab), cudaMemcpyHostToDevice, s));
-    CK(launch_build_slots(net->d_words, net->d_seg, net->d_part_lo, net->d_wtab, net->n, net->P,
-                          net->n_pop, net->pop_start, net->ncmax, net->d_slot_base, net->d_slot_S,
-                          net->d_slots, s));
     CK(cudaStreamSynchronize(s));
     return SNN_OK;
+}
+
+int partition_pop_span(const int32_t* part_lo, int n_part, const int32_t* pop_start, int n_pop) {
+    auto pop_of = [&](int32_t i) {
+        int p = 0;
+        while (p + 1 < n_pop && i >= pop_start[p + 1]) ++p;
+        return p;
+    };
+    int span = 1;
+    for (int c = 0; c < n_part; ++c)
+        if (part_lo[c + 1] > part_lo[c])
+            span = std::max(span, pop_of(part_lo[c + 1] - 1) - pop_of(part_lo[c]) + 1);
+    return span;
 }
 
 int set_error(int code, const char* msg) { return fail(code, msg); }
@@ -814,8 +814,8 @@ int snn_get_info(snn_net* net, snn_info* info) {
     for (int k = 0; k < 4; ++k) info->propagators[k] = net->prop[k];
     info->wext_q = net->wext_q;
     info->shared_bytes = (int32_t)net->smem;
-    info->slot_entries = net->slot_entries;
-    info->slot_bytes = (int64_t)(net->slot_total * sizeof(int2));
+    info->slot_entries = net->run_max;
+    info->slot_bytes = (int64_t)(net->nnz * sizeof(uint32_t));
     int active = 0;
     if (deliver_cluster_check(net->ncmax, net->P, &active) != cudaSuccess) {
         cudaGetLastError();
@@ -872,12 +872,6 @@ int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int6
         }
         CK(launch_deliver_cluster(dp, net->stream));
     } else if (tiling == 3) {
-        if (!net->d_pre) {          // pre-decoded rows, built on first use
-            if ((long long)kRing * net->ncmax >= (long long)kPreOffMask)
-                return fail(SNN_ERR_UNSUPPORTED, "ring slices too large for the partition-word delivery");
-            CALL(dalloc(&net->d_pre, (size_t)net->nnz + 4, "pre-decoded rows"));
-            CK(launch_predecode(dp, net->d_row_start, net->d_pre, net->stream));
-        }
         dp.pre = net->d_pre;
         CK(launch_deliver_words(dp, net->stream));
     } else {

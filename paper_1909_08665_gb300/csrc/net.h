@@ -39,18 +39,15 @@ struct snn_net {
     unsigned long long* d_row_start = nullptr;
     uint32_t* d_seg = nullptr;
     uint32_t* d_words = nullptr;
-    uint32_t* d_pre = nullptr;              // rows pre-decoded for the partition-word delivery (first use)
+    uint32_t* d_pre = nullptr;              // rows pre-decoded (weight-table index, ring offset)
     int32_t* d_wtab = nullptr;
     uint8_t* d_dtab = nullptr;
     float* d_u = nullptr;
     float* d_i = nullptr;
     int32_t* d_r = nullptr;
     int32_t* d_ring = nullptr;
-    int2* d_slots = nullptr;               // partition c: [n][S_c] (weight, ring offset)
-    unsigned long long* d_slot_base = nullptr;  // [P] first entry of partition c
-    uint32_t* d_slot_S = nullptr;          // [P] S_c = entries per slot of partition c
-    int32_t slot_entries = 0;              // largest S_c
-    uint64_t slot_total = 0;               // entries allocated
+    int32_t w_span = 1;                    // target populations of the widest partition
+    int32_t run_max = 0;                   // longest (row, partition) run
     unsigned long long* d_msg = nullptr;   // [4][P][msg_stride] tagged spike messages
     int32_t msg_stride = 0;
     uint32_t* d_ras_step = nullptr;
@@ -76,7 +73,7 @@ namespace snn {
 void fill_step_params(const snn_net* net, StepParams* sp);
 // recompute the weight, delay, Poisson and propagator tables from net->cfg
 int net_make_tables(snn_net* net);
-// upload the weight table and rebuild the delivery slots from it
+// upload the weight table (the step kernel stages it at launch)
 int net_upload_weights(snn_net* net);
 // launch the step kernel for n steps from step t0 with the given parameters
 cudaError_t net_launch(snn_net* net, StepParams& sp, int64_t t0, int64_t n);

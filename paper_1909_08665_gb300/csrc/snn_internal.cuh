@@ -130,10 +130,6 @@ struct BuildParams {
     const int32_t* part_lo;             // device [n_part + 1]
 };
 
-struct SlotPops {
-    int32_t pop_start[kMaxPop + 1];
-};
-
 // model constants and tables of one configuration, computed on the host
 struct HostTables {
     int32_t n, n_pop;
@@ -159,17 +155,15 @@ struct StepParams {
     uint64_t timeout_ns;
     int32_t inject_fault;               // 1: partition 0 never publishes
     int32_t msg_stride;                 // 64-bit words per message (>= ncmax + 1)
-    int32_t pad_slots;
+    int32_t w_span;                     // target populations of the widest partition
     uint32_t pois_m1[kMaxPop][kPoisTable];  // Poisson thresholds minus 1 (x > T-1 -> +1)
     // network (read only)
     const int32_t* part_lo;             // [n_part + 1]
     const uint32_t* seg;                // [n][n_part + 1] absolute word offsets
     const uint32_t* words;
+    const uint32_t* pre;                // pre-decoded rows, same layout as words
     const int32_t* wtab;                // [8][8][128]
     const unsigned long long* row_start;  // [n + 1] row offsets
-    const int2* slots;                  // partition c: [n][slot_S[c]] (weight, ring offset) at slot_base[c]
-    const unsigned long long* slot_base;  // [n_part] first entry of each partition's slots
-    const uint32_t* slot_S;             // [n_part] entries per slot (power of 2, >= 32)
     // state
     float* u;
     float* i_syn;
@@ -237,11 +231,6 @@ cudaError_t launch_seg_from_rows(const unsigned long long* row_start, const uint
 // out[c] = longest (row, partition c) segment, for every partition c
 cudaError_t launch_max_segment(const uint32_t* seg, int n, int n_part, uint32_t* out,
                                cudaStream_t s);
-cudaError_t launch_build_slots(const uint32_t* words, const uint32_t* seg, const int32_t* part_lo,
-                               const int32_t* wtab, int n, int n_part, int n_pop,
-                               const int32_t* pop_start, int ncmax,
-                               const unsigned long long* slot_base, const uint32_t* slot_S,
-                               int2* slots, cudaStream_t s);
 // the raster entries of every partition (counts clamped to cap_part, then the
 // first `limit` entries in partition order) packed into step_out / id_out
 cudaError_t launch_pack_raster(const uint32_t* counts, int n_part, uint32_t cap_part,
@@ -250,7 +239,10 @@ cudaError_t launch_pack_raster(const uint32_t* counts, int n_part, uint32_t cap_
 cudaError_t launch_init_state(int n, uint32_t key0, uint32_t key1, float lo, float hi,
                               float* u, cudaStream_t s);
 int step_kernel_variant(int npt, bool smem_ring);
-size_t step_shared_bytes(int ncmax, int n_part, bool smem_ring);
+size_t step_shared_bytes(int ncmax, int n_part, int w_span, bool smem_ring);
+// target populations spanned by the widest of the partitions [part_lo[c],
+// part_lo[c+1]) (the rows of the weight table a CTA of the step kernel keeps)
+int partition_pop_span(const int32_t* part_lo, int n_part, const int32_t* pop_start, int n_pop);
 cudaError_t step_kernel_configure(int npt, bool smem_ring, size_t smem);
 cudaError_t launch_step(const StepParams& sp, int npt, bool smem_ring, size_t smem,
                         cudaStream_t s);
@@ -270,7 +262,7 @@ cudaError_t launch_predecode(const DeliverParams& dp, const unsigned long long* 
 // shared memory); needs the ring slice and the weight table in shared memory
 cudaError_t launch_deliver_cluster(const DeliverParams& dp, cudaStream_t s);
 cudaError_t deliver_cluster_check(int ncmax, int n_part, int* max_active_clusters);
-// stand-alone delivery through the partition slots (one CTA per partition)
+// stand-alone delivery through the step kernel's runs (one CTA per partition)
 cudaError_t launch_deliver_part(const StepParams& sp, const uint32_t* spikes, int n, int64_t t,
                                 bool smem_ring, cudaStream_t s);
 

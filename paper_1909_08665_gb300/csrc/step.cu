@@ -4,25 +4,29 @@
 // One persistent cooperative launch runs n steps.  CTA c owns the neuron
 // range [part_lo[c], part_lo[c+1]): their state lives in registers and their
 // 64-slot synaptic-input ring buffers live in shared memory (or in a
-// partition-private global block when they do not fit).  Besides the plain
-// rows, every row j has one fixed-size slot per partition c holding the count
-// and the synapses of j onto c as (fixed-point weight, ring offset) pairs, so
-// CTA c reads exactly its own synapses of a spike with one coalesced load, no
-// offset lookup and no table lookup, and adds them with shared-memory atomics.
-// (A producer-side L2 prefetch of the rows of emitted spikes was measured and
-// gave no gain once the slots are read in one round trip, so there is none.)
+// partition-private global block when they do not fit).  Rows are sorted by
+// target and partitions are contiguous neuron ranges, so the synapses of row
+// j onto partition c are one contiguous run of the row, [seg[j][c],
+// seg[j][c+1]).  CTA c reads exactly that run of every spike's row -- 4 bytes
+// per synaptic event, the algorithmic minimum -- from a pre-decoded copy of
+// the rows whose entries carry the weight-table index and the offset of the
+// target's ring cell in its partition's slice, and adds the weights (looked
+// up in a shared-memory copy of the table rows its populations use) with
+// shared-memory atomics.  The run bounds come from the segment table, which
+// the CTA reads for each spike while it gathers the step's spike ids, so that
+// lookup overlaps the wait for the slowest partition's message.
 //
 // Per step t the order is:
 //   A(t)  u_t from (u_{t-1}, I_{t-1}); threshold, reset, refractory; the
 //         spikes of step t are compacted with warp ballots and published as
 //         a message of 64-bit words (tag = t+1, value) -- the count and the
-//         neuron ids -- and the rows of those neurons are prefetched to L2;
-//         the Poisson background count of step t is drawn.
+//         neuron ids; the Poisson background count of step t is drawn.
 //   D     wait for every partition's message of step t-1 (each word carries
 //         its own tag, so a matching tag is both the grid-wide barrier and
-//         the data; no fence, no counter) and deliver those spikes into ring
-//         slots t-1+d (d >= 1): per warp, batches of 4 spikes whose segment
-//         bounds and words are all loaded before the shared-memory atomics.
+//         the data; no fence, no counter), look up each spike's run for this
+//         partition and deliver those spikes into ring slots t-1+d (d >= 1):
+//         per warp, batches of 4 spikes whose runs are all loaded before the
+//         shared-memory atomics.
 //   C(t)  acc = ring[t] (cleared) + background; I_t = P11 I_{t-1} + acc/256.
 // A(t+1) needs only I_t, and the spikes of step t reach no input before
 // slot t+1, so the spike exchange of one step overlaps the next step's
@@ -39,27 +43,33 @@ namespace snn {
 
 constexpr int kWarps = kStepThreads / 32;
 constexpr uint32_t kStatusRasterOverflow = 2u;
-constexpr int kInline = 7;
-constexpr int kSlotWave = 4;            // slot entries per lane loaded at once (128 per slot)        // ids read together with a message header (64 B)
+constexpr int kInline = 7;              // ids read together with a message header (64 B)
+constexpr int kRunWave = 4;             // run entries per lane loaded at once (128 per spike)
+constexpr uint32_t kPopWords = kMaxPop * kWCodes;   // weight-table entries per target population
 
 // ---------------------------------------------------------------------------
 // shared-memory layout (bytes), identical on host and device
 // ---------------------------------------------------------------------------
 struct SmemLayout {
-    uint32_t pois, warp, misc, cntoff, inl, spk, ring, total;
+    uint32_t pois, warp, misc, inl, rb, rl, w, ring, total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(int ncmax, int n_part, bool smem_ring) {
+// s_rb / s_rl: first entry and length of each listed spike's run; s_w: the
+// weight-table rows [p][q][code] of the w_span target populations from the
+// partition's first one on
+__host__ __device__ inline SmemLayout smem_layout(int ncmax, int n_part, int w_span,
+                                                  bool smem_ring) {
     SmemLayout L;
     uint32_t o = 0;
     L.pois = o;   o += kMaxPop * kPoisTable * 4;
     L.warp = o;   o += 32 * 4;
     L.misc = o;   o += 32 * 4;
-    L.cntoff = o; o = align_up(o + (uint32_t)(n_part + 1) * 4, 16);
     L.inl = o;    o += (uint32_t)n_part * kInline * 8;
-    L.spk = o;    o += kChunk * 4;
+    L.rb = o;     o += kChunk * 4;
+    L.rl = o;     o += kChunk * 4;
+    L.w = o;      o += (uint32_t)w_span * kPopWords * 4;
     L.ring = o;
     if (smem_ring) o += (uint32_t)kRing * (uint32_t)ncmax * 4;
     L.total = o;
@@ -129,58 +139,82 @@ __device__ bool poll_word(const StepParams& sp, const unsigned long long* p, uin
 }
 
 // ---------------------------------------------------------------------------
-// the spikes s_spk[0, m) of step tb into this CTA's ring: batches of 4 spikes
-// per warp.  The slot of (spike, this partition) holds the count and the
-// synapses as (weight, ring offset) pairs; each lane loads entries lane and
-// lane+32 of all 4 slots (all loads in flight at once), then adds each weight
-// at (tb mod 64) * ncmax + offset, wrapped into the 64-slot ring.
+// the runs s_rb/s_rl[0, m) of the spikes of step tb into this CTA's ring:
+// batches of 4 spikes per warp.  Entry x of a run (a pre-decoded synapse) is
+// the weight-table index x >> kPreOffBits and the ring offset
+// x & kPreOffMask = delay * ncmax + local target; its weight, looked up in
+// s_w (table rows from population p_lo on, wbase = p_lo * kPopWords), is
+// added at ((tb mod 64) * ncmax + offset) wrapped into the 64-slot ring.  Each
+// lane loads entries lane + 32 h (h < kRunWave) of all 4 runs before the
+// first add (all loads in flight at once); longer runs finish in a loop.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void deliver_batches(const StepParams& sp, const uint32_t* s_spk,
-                                                uint32_t m, int c, int64_t tb, int32_t* ring,
-                                                unsigned long long& events) {
+__device__ __forceinline__ void add_entry(uint32_t x, const int32_t* s_w, uint32_t wbase,
+                                          int32_t base_t, int32_t R, int32_t* ring) {
+    const int32_t w = s_w[(x >> kPreOffBits) - wbase];
+    int32_t a = base_t + (int32_t)(x & kPreOffMask);
+    a -= a >= R ? R : 0;
+    atomicAdd(&ring[a], w);
+}
+
+__device__ __forceinline__ void deliver_batches(const StepParams& sp, const uint32_t* s_rb,
+                                                const uint32_t* s_rl, const int32_t* s_w,
+                                                uint32_t wbase, uint32_t m, int64_t tb,
+                                                int32_t* ring, unsigned long long& events) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // this partition's slots: stride S_c entries, the first min(S_c, 128)
-    // of each slot loaded in one wave (NE entries per lane)
-    const uint32_t S_c = __ldg(&sp.slot_S[c]);
-    const int2* sbase = sp.slots + __ldg(&sp.slot_base[c]);
-    const uint32_t NE = min(S_c >> 5, (uint32_t)kSlotWave);
     const int32_t R = kRing * sp.ncmax;                  // ring words of this CTA
     const int32_t base_t = (int32_t)(((uint32_t)tb & (kRing - 1)) * (uint32_t)sp.ncmax);
+    const uint32_t* pre = sp.pre;
     for (uint32_t g0 = (uint32_t)warp * 4u; g0 < m; g0 += (uint32_t)kWarps * 4u) {
-        const int2* sl[4];
-        int2 ev[4][kSlotWave];
+        uint32_t rb[4], rl[4];
+        uint32_t ev[4][kRunWave];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const bool ok = g0 + (uint32_t)k < m;
-            const uint32_t id = ok ? s_spk[g0 + k] : 0u;
-            sl[k] = sbase + (size_t)id * S_c;
+            rb[k] = ok ? s_rb[g0 + k] : 0u;
+            rl[k] = ok ? s_rl[g0 + k] : 0u;
 #pragma unroll
-            for (int h = 0; h < kSlotWave; ++h)
-                ev[k][h] = (ok && (uint32_t)h < NE) ? __ldg(sl[k] + 32 * h + lane) : make_int2(0, 0);
+            for (int h = 0; h < kRunWave; ++h) {
+                const uint32_t e = (uint32_t)lane + 32u * (uint32_t)h;
+                ev[k][h] = e < rl[k] ? __ldg(pre + ((size_t)rb[k] + e)) : 0u;
+            }
         }
-        // entry 0 of a slot is its count; entry e >= 1 is (weight, offset)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const uint32_t cnt = (uint32_t)__shfl_sync(0xffffffffu, ev[k][0].x, 0);
 #pragma unroll
-            for (int h = 0; h < kSlotWave; ++h) {
-                const uint32_t e = (uint32_t)lane + 32u * (uint32_t)h;
-                if ((uint32_t)h < NE && e >= 1u && e <= cnt) {
-                    int32_t a = base_t + ev[k][h].y;
-                    a -= a >= R ? R : 0;
-                    atomicAdd(&ring[a], ev[k][h].x);
-                }
-            }
-            // entries beyond the first wave (partitions with S_c > 32 kSlotWave)
-            for (uint32_t e = 32u * NE + (uint32_t)lane; e <= cnt; e += 32u) {
-                const int2 x = __ldg(sl[k] + e);
-                int32_t a = base_t + x.y;
-                a -= a >= R ? R : 0;
-                atomicAdd(&ring[a], x.x);
-            }
-            if (lane == 0) events += cnt;
+            for (int h = 0; h < kRunWave; ++h)
+                if ((uint32_t)lane + 32u * (uint32_t)h < rl[k])
+                    add_entry(ev[k][h], s_w, wbase, base_t, R, ring);
+            // entries beyond the first wave (runs longer than 32 kRunWave)
+            for (uint32_t e = 32u * kRunWave + (uint32_t)lane; e < rl[k]; e += 32u)
+                add_entry(__ldg(pre + ((size_t)rb[k] + e)), s_w, wbase, base_t, R, ring);
+            if (lane == 0) events += rl[k];
         }
     }
+}
+
+// Runs of this partition c for the N spike ids ids[0, cnt): both bounds of
+// every id are loaded before any is stored, so the lookups are in flight
+// together; a run is written as (first entry, length).
+template <int N>
+__device__ __forceinline__ void store_runs(const StepParams& sp, int c, const uint32_t (&ids)[N],
+                                           uint32_t cnt, uint32_t* o_rb, uint32_t* o_rl) {
+    uint32_t b[N], e[N];
+    const size_t stride = (size_t)sp.n_part + 1;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        b[k] = e[k] = 0u;
+        if ((uint32_t)k < cnt) {
+            const uint32_t* sg = sp.seg + (size_t)ids[k] * stride + c;
+            b[k] = __ldg(sg);
+            e[k] = __ldg(sg + 1);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        if ((uint32_t)k < cnt) {
+            o_rb[k] = b[k];
+            o_rl[k] = e[k] - b[k];
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -188,7 +222,7 @@ __device__ __forceinline__ void deliver_batches(const StepParams& sp, const uint
 // returns false if a wait timed out or another CTA aborted
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char* smem,
-                                             const SmemLayout& L, int c, int32_t lo,
+                                             const SmemLayout& L, int c, uint32_t wbase,
                                              int64_t tb, int32_t* ring,
                                              unsigned long long& events,
                                              const ulonglong2 (&pre)[4]) {
@@ -199,7 +233,9 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
     uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + L.warp);
     volatile uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + L.misc);
     unsigned long long* s_inl = reinterpret_cast<unsigned long long*>(smem + L.inl);
-    uint32_t* s_spk = reinterpret_cast<uint32_t*>(smem + L.spk);
+    uint32_t* s_rb = reinterpret_cast<uint32_t*>(smem + L.rb);
+    uint32_t* s_rl = reinterpret_cast<uint32_t*>(smem + L.rl);
+    const int32_t* s_w = reinterpret_cast<const int32_t*>(smem + L.w);
     const unsigned long long* msg = sp.msg + (size_t)list * P * sp.msg_stride;
 
     // 1. every partition's 64-byte message head: the header word (the wait and
@@ -239,18 +275,23 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
     }
     const uint32_t my_cnt = cnt[0];
     // 2a. usual case, one barrier: each header reader appends its partition's
-    //     ids to the shared list at a position taken from a shared counter;
-    //     ids beyond the inline ones are loaded 8 at a time, all in flight
+    //     runs to the shared list at a position taken from a shared counter;
+    //     ids beyond the inline ones are loaded 8 at a time, all in flight,
+    //     and the run bounds of a group of ids are looked up together
     if (tid < P && my_cnt > 0u) {
         const uint32_t at = atomicAdd(const_cast<uint32_t*>(&s_misc[3]), my_cnt);
         if (at + my_cnt <= (uint32_t)kChunk) {
-            for (uint32_t i = 0; i < my_cnt && i < (uint32_t)kInline; ++i) {
-                unsigned long long e = s_inl[tid * kInline + i];
-                uint32_t id = 0u;                    // in range if a wait gives up
-                if (poll_word(sp, m_mine + 1 + i, tag, e)) id = (uint32_t)e;
-                else s_misc[2] = 1u;
-                s_spk[at + i] = id;
+            uint32_t ids[kInline];
+#pragma unroll
+            for (int i = 0; i < kInline; ++i) {
+                ids[i] = 0u;                         // in range if a wait gives up
+                if ((uint32_t)i < my_cnt) {
+                    unsigned long long e = s_inl[tid * kInline + i];
+                    if (poll_word(sp, m_mine + 1 + i, tag, e)) ids[i] = (uint32_t)e;
+                    else s_misc[2] = 1u;
+                }
             }
+            store_runs<kInline>(sp, c, ids, min(my_cnt, (uint32_t)kInline), s_rb + at, s_rl + at);
             for (uint32_t i = kInline; i < my_cnt; i += 8) {
                 ulonglong2 v[4];                     // entries 1+i.. are 16-B aligned
 #pragma unroll
@@ -258,17 +299,18 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
                     v[q] = i + 2 * q < my_cnt
                                ? __ldcg(reinterpret_cast<const ulonglong2*>(m_mine + 1 + i + 2 * q))
                                : make_ulonglong2(0ull, 0ull);
+                uint32_t ids8[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const uint32_t k = i + (uint32_t)q;
+                    ids8[q] = 0u;
                     if (k < my_cnt) {
                         unsigned long long e = (q & 1) ? v[q >> 1].y : v[q >> 1].x;
-                        uint32_t id = 0u;
-                        if (poll_word(sp, m_mine + 1 + k, tag, e)) id = (uint32_t)e;
+                        if (poll_word(sp, m_mine + 1 + k, tag, e)) ids8[q] = (uint32_t)e;
                         else s_misc[2] = 1u;
-                        s_spk[at + k] = id;
                     }
                 }
+                store_runs<8>(sp, c, ids8, min(my_cnt - i, 8u), s_rb + at + i, s_rl + at + i);
             }
         }
     }
@@ -276,7 +318,7 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
     const uint32_t S_fast = s_misc[3];
     if (s_misc[2]) return false;
     if (S_fast <= (uint32_t)kChunk) {
-        deliver_batches(sp, s_spk, S_fast, c, tb, ring, events);
+        deliver_batches(sp, s_rb, s_rl, s_w, wbase, S_fast, tb, ring, events);
         __syncthreads();
         if (tid == 0) s_misc[3] = 0u;
         return s_misc[2] == 0u;
@@ -288,23 +330,31 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
 
     for (uint32_t base = 0; base < S; base += kChunk) {
         const uint32_t m = min((uint32_t)kChunk, S - base);
-        // 2. the spike ids of this chunk into a shared list, each partition's
-        //    ids written by the thread that read its header
+        // 2. the runs of this chunk into the shared list, each partition's
+        //    written by the thread that read its header, 8 ids at a time
         if (tid < P) {
             // this partition's ids i with base <= my_off + i < base + m
             const uint32_t i0 = base > my_off ? base - my_off : 0u;
             const uint32_t i1 = base + m > my_off ? min(my_cnt, base + m - my_off) : 0u;
-            for (uint32_t i = i0; i < i1; ++i) {
-                const unsigned long long* mp = m_mine + 1 + i;
-                unsigned long long e = i < (uint32_t)kInline ? s_inl[tid * kInline + i] : __ldcg(mp);
-                uint32_t id = 0u;                    // in range if a wait gives up
-                if (poll_word(sp, mp, tag, e)) id = (uint32_t)e;
-                else s_misc[2] = 1u;
-                s_spk[my_off + i - base] = id;
+            for (uint32_t i = i0; i < i1; i += 8) {
+                uint32_t ids8[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t k = i + (uint32_t)q;
+                    ids8[q] = 0u;                    // in range if a wait gives up
+                    if (k < i1) {
+                        const unsigned long long* mp = m_mine + 1 + k;
+                        unsigned long long e = k < (uint32_t)kInline ? s_inl[tid * kInline + k] : __ldcg(mp);
+                        if (poll_word(sp, mp, tag, e)) ids8[q] = (uint32_t)e;
+                        else s_misc[2] = 1u;
+                    }
+                }
+                const uint32_t o = my_off + i - base;
+                store_runs<8>(sp, c, ids8, min(i1 - i, 8u), s_rb + o, s_rl + o);
             }
         }
         __syncthreads();
-        deliver_batches(sp, s_spk, m, c, tb, ring, events);
+        deliver_batches(sp, s_rb, s_rl, s_w, wbase, m, tb, ring, events);
         __syncthreads();
     }
     return s_misc[2] == 0u;
@@ -323,9 +373,10 @@ k_step(const __grid_constant__ StepParams sp) {
     const int lane = tid & 31;
     const int c = blockIdx.x;
     const int P = sp.n_part;
-    const SmemLayout L = smem_layout(sp.ncmax, P, SMEM_RING);
+    const SmemLayout L = smem_layout(sp.ncmax, P, sp.w_span, SMEM_RING);
     uint32_t* s_pois = reinterpret_cast<uint32_t*>(smem + L.pois);
     uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + L.misc);
+    int32_t* s_w = reinterpret_cast<int32_t*>(smem + L.w);
 
     const int32_t lo = sp.part_lo[c];
     const int32_t nc = sp.part_lo[c + 1] - lo;
@@ -335,6 +386,11 @@ k_step(const __grid_constant__ StepParams sp) {
 
     for (int k = tid; k < kMaxPop * kPoisTable; k += kStepThreads)
         s_pois[k] = sp.pois_m1[k / kPoisTable][k % kPoisTable];
+    // weight-table rows of the target populations of this partition: those
+    // from the population of its first neuron on (at most w_span of them)
+    const uint32_t wbase = (uint32_t)pop_index(sp.pop_start, sp.n_pop, lo) * kPopWords;
+    for (uint32_t k = tid; k < (uint32_t)sp.w_span * kPopWords; k += kStepThreads)
+        s_w[k] = wbase + k < (uint32_t)(kMaxPop * kPopWords) ? __ldg(&sp.wtab[wbase + k]) : 0;
     if (SMEM_RING)
         for (int k = tid; k < kRing * sp.ncmax; k += kStepThreads) ring[k] = ring_g[k];
     if (tid < 32) s_misc[tid] = 0u;
@@ -460,7 +516,7 @@ k_step(const __grid_constant__ StepParams sp) {
         ras_base += nsp;
         // ---- D: spikes of step t-1 ----
         if (s > 0) {
-            if (!deliver_list(sp, smem, L, c, lo, t - 1, ring, events, pre)) {
+            if (!deliver_list(sp, smem, L, c, wbase, t - 1, ring, events, pre)) {
                 aborted = true;
                 break;
             }
@@ -507,7 +563,7 @@ k_step(const __grid_constant__ StepParams sp) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) pre[q] = __ldcg(reinterpret_cast<const ulonglong2*>(m + 2 * q));
         }
-        deliver_list(sp, smem, L, c, lo, tl, ring, events, pre);
+        deliver_list(sp, smem, L, c, wbase, tl, ring, events, pre);
     }
     __syncthreads();
 #pragma unroll
@@ -584,8 +640,8 @@ __global__ void __launch_bounds__(256) k_deliver_block(const __grid_constant__ D
 // ---------------------------------------------------------------------------
 // host-side helpers
 // ---------------------------------------------------------------------------
-size_t step_shared_bytes(int ncmax, int n_part, bool smem_ring) {
-    return smem_layout(ncmax, n_part, smem_ring).total;
+size_t step_shared_bytes(int ncmax, int n_part, int w_span, bool smem_ring) {
+    return smem_layout(ncmax, n_part, w_span, smem_ring).total;
 }
 
 template <int NPT, bool R>
@@ -643,27 +699,45 @@ cudaError_t launch_step(const StepParams& sp, int npt, bool smem_ring, size_t sm
 }
 
 // Partition tiling of the stand-alone delivery: CTA c takes every spike of
-// the list through its partition slots (the step kernel's delivery), with its
-// ring slice staged in shared memory when it fits.
+// the list through its runs of the pre-decoded rows (the step kernel's
+// delivery), with its ring slice staged in shared memory when it fits.
+// Shared memory: run starts and lengths [kChunk] each, the weight-table rows
+// of the partition's populations, then the ring slice.
+__host__ __device__ inline size_t part_smem_bytes(int ncmax, int w_span, bool smem_ring) {
+    return (size_t)kChunk * 8 + (size_t)w_span * kPopWords * 4 +
+           (smem_ring ? (size_t)kRing * ncmax * 4 : 0);
+}
+
 template <bool SMEM_RING>
 __global__ void __launch_bounds__(kStepThreads, 1)
 k_deliver_part(const __grid_constant__ StepParams sp, const uint32_t* __restrict__ spikes, int n,
                int64_t t) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* s_spk = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* s_rb = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* s_rl = s_rb + kChunk;
+    int32_t* s_w = reinterpret_cast<int32_t*>(s_rl + kChunk);
     const int c = blockIdx.x, tid = threadIdx.x;
     const int R = kRing * sp.ncmax;
     int32_t* ring_g = sp.ring + (size_t)c * R;
-    int32_t* ring = SMEM_RING ? reinterpret_cast<int32_t*>(s_spk + kChunk) : ring_g;
+    int32_t* ring = SMEM_RING ? s_w + (size_t)sp.w_span * kPopWords : ring_g;
+    const uint32_t wbase = (uint32_t)pop_index(sp.pop_start, sp.n_pop, sp.part_lo[c]) * kPopWords;
+    for (uint32_t k = tid; k < (uint32_t)sp.w_span * kPopWords; k += kStepThreads)
+        s_w[k] = wbase + k < (uint32_t)(kMaxPop * kPopWords) ? __ldg(&sp.wtab[wbase + k]) : 0;
     if (SMEM_RING)
         for (int k = tid; k < R; k += kStepThreads) ring[k] = ring_g[k];
     __syncthreads();
     unsigned long long events = 0;
+    const size_t stride = (size_t)sp.n_part + 1;
     for (int base = 0; base < n; base += kChunk) {
         const int m = min(kChunk, n - base);
-        for (int k = tid; k < m; k += kStepThreads) s_spk[k] = __ldg(&spikes[base + k]);
+        for (int k = tid; k < m; k += kStepThreads) {
+            const uint32_t* sg = sp.seg + (size_t)__ldg(&spikes[base + k]) * stride + c;
+            const uint32_t b = __ldg(sg);
+            s_rb[k] = b;
+            s_rl[k] = __ldg(sg + 1) - b;
+        }
         __syncthreads();
-        deliver_batches(sp, s_spk, (uint32_t)m, c, t, ring, events);
+        deliver_batches(sp, s_rb, s_rl, s_w, wbase, (uint32_t)m, t, ring, events);
         __syncthreads();
     }
     if (SMEM_RING)
@@ -674,10 +748,16 @@ k_deliver_part(const __grid_constant__ StepParams sp, const uint32_t* __restrict
 cudaError_t launch_deliver_part(const StepParams& sp, const uint32_t* spikes, int n, int64_t t,
                                 bool smem_ring, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const size_t smem = (size_t)kChunk * 4 + (smem_ring ? (size_t)kRing * sp.ncmax * 4 : 0);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    smem_ring = smem_ring && part_smem_bytes(sp.ncmax, sp.w_span, true) <= (size_t)optin;
+    const size_t smem = part_smem_bytes(sp.ncmax, sp.w_span, smem_ring);
     const void* fn = smem_ring ? reinterpret_cast<const void*>(&k_deliver_part<true>)
                                : reinterpret_cast<const void*>(&k_deliver_part<false>);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (smem_ring)
         k_deliver_part<true><<<sp.n_part, kStepThreads, smem, s>>>(sp, spikes, n, t);
