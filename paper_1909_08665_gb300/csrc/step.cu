@@ -360,6 +360,22 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
     return s_misc[2] == 0u;
 }
 
+// Bulk prefetch of [addr, addr + bytes) into L2 (16-byte aligned, multiple
+// of 16 bytes): fire and forget.
+__device__ __forceinline__ void prefetch_l2(unsigned long long addr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(addr), "r"(bytes) : "memory");
+}
+
+// 16-byte-aligned span covering the 4-byte words [b, e) of base
+__device__ __forceinline__ void span16(const uint32_t* base, unsigned long long b,
+                                       unsigned long long e, unsigned long long& addr,
+                                       uint32_t& bytes) {
+    const unsigned long long lo = reinterpret_cast<unsigned long long>(base + b) & ~15ull;
+    const unsigned long long hi = (reinterpret_cast<unsigned long long>(base + e) + 15ull) & ~15ull;
+    addr = lo;
+    bytes = e > b ? (uint32_t)(hi - lo) : 0u;
+}
+
 // ---------------------------------------------------------------------------
 // persistent step kernel
 // ---------------------------------------------------------------------------
@@ -388,9 +404,9 @@ k_step(const __grid_constant__ StepParams sp) {
         s_pois[k] = sp.pois_m1[k / kPoisTable][k % kPoisTable];
     // weight-table rows of the target populations of this partition: those
     // from the population of its first neuron on (at most w_span of them)
-    const uint32_t wbase = (uint32_t)pop_index(sp.pop_start, sp.n_pop, lo) * kPopWords;
+    const uint32_t wt_base = (uint32_t)pop_index(sp.pop_start, sp.n_pop, lo) * kPopWords;
     for (uint32_t k = tid; k < (uint32_t)sp.w_span * kPopWords; k += kStepThreads)
-        s_w[k] = wbase + k < (uint32_t)(kMaxPop * kPopWords) ? __ldg(&sp.wtab[wbase + k]) : 0;
+        s_w[k] = wt_base + k < (uint32_t)(kMaxPop * kPopWords) ? __ldg(&sp.wtab[wt_base + k]) : 0;
     if (SMEM_RING)
         for (int k = tid; k < kRing * sp.ncmax; k += kStepThreads) ring[k] = ring_g[k];
     if (tid < 32) s_misc[tid] = 0u;
@@ -403,16 +419,30 @@ k_step(const __grid_constant__ StepParams sp) {
     int32_t refr[NPT], pacc[NPT];
     int pop[NPT];
     uint4 rnd[NPT];
+    // the neuron's own row of the pre-decoded rows and of the segment table,
+    // prefetched into L2 when it spikes: every partition reads its run of
+    // that row one step later (NPT <= 4: the registers of the widest
+    // variant are spent elsewhere)
+    constexpr int NPF = NPT <= 4 ? NPT : 1;
+    unsigned long long pf_row[NPF], pf_seg[NPF];
+    uint32_t pf_row_n[NPF], pf_seg_n[NPF];
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
         const int li = tid + k * kStepThreads;
         u[k] = 0.f; isyn[k] = 0.f; refr[k] = 0; pop[k] = 0; pacc[k] = 0;
         rnd[k] = make_uint4(0u, 0u, 0u, 0u);
+        if (k < NPF) { pf_row[k] = pf_seg[k] = 0ull; pf_row_n[k] = pf_seg_n[k] = 0u; }
         if (li < nc) {
             u[k] = sp.u[lo + li];
             isyn[k] = sp.i_syn[lo + li];
             refr[k] = sp.refr[lo + li];
             pop[k] = pop_index(sp.pop_start, sp.n_pop, lo + li);
+            if (NPT <= 4 && k < NPF) {
+                const unsigned long long j = (unsigned long long)(lo + li);
+                span16(sp.pre, sp.row_start[j], sp.row_start[j + 1], pf_row[k], pf_row_n[k]);
+                const unsigned long long sw = j * (unsigned long long)(P + 1);
+                span16(sp.seg, sw, sw + (unsigned long long)(P + 1), pf_seg[k], pf_seg_n[k]);
+            }
         }
     }
     uint32_t ras_base = sp.ras_n[c];
@@ -476,6 +506,10 @@ k_step(const __grid_constant__ StepParams sp) {
                     const uint32_t pos = wbase + (uint32_t)__popc(mask & ((1u << lane) - 1u));
                     const uint32_t id = (uint32_t)(lo + li);
                     __stcg(&my_msg[1 + pos], tag | id);
+                    if (NPT <= 4 && k < NPF) {
+                        if (pf_row_n[k]) prefetch_l2(pf_row[k], pf_row_n[k]);
+                        prefetch_l2(pf_seg[k], pf_seg_n[k]);
+                    }
                     const uint32_t rp = ras_base + pos;
                     if (rp < sp.ras_cap) {
                         sp.ras_step[(size_t)c * sp.ras_cap + rp] = (uint32_t)t;
@@ -516,7 +550,7 @@ k_step(const __grid_constant__ StepParams sp) {
         ras_base += nsp;
         // ---- D: spikes of step t-1 ----
         if (s > 0) {
-            if (!deliver_list(sp, smem, L, c, wbase, t - 1, ring, events, pre)) {
+            if (!deliver_list(sp, smem, L, c, wt_base, t - 1, ring, events, pre)) {
                 aborted = true;
                 break;
             }
@@ -563,7 +597,7 @@ k_step(const __grid_constant__ StepParams sp) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) pre[q] = __ldcg(reinterpret_cast<const ulonglong2*>(m + 2 * q));
         }
-        deliver_list(sp, smem, L, c, wbase, tl, ring, events, pre);
+        deliver_list(sp, smem, L, c, wt_base, tl, ring, events, pre);
     }
     __syncthreads();
 #pragma unroll
