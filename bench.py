@@ -20,6 +20,12 @@ Printed JSON line (rank 0):
 --impl reference times the CPU oracle itself (the reference arm).
 Multi-GPU (torchrun, --gpus N): N independent replicas, one per GPU.
 
+The default line also carries, each with its own device timing, roofline and
+clock record (skipped with --no-extras): deliver_20000 (the partition-word
+delivery of 20,000-spike lists at scale 1), scale4 (1 s biological of the 4x
+network), batch64 (1 s biological of 64 instances) and grad_config3 (one
+forward + backward of the 10 % network over 200 ms).
+
 Other workloads (--workload; the default line is the full microcircuit):
   scale4  the 4x microcircuit (308,676 neurons, ~1.2e9 synapses), same metric
   batch   64 independent microcircuits at scales U(0.05, 0.25) in one
@@ -53,10 +59,10 @@ UNIT = "synaptic events/s"
 STEPS_PER_BENCH_STEP = 10000          # 1 s of biological time at dt = 0.1 ms
 BYTES_PER_EVENT = 4                   # one packed synaptic word read per event
 # DRAM bytes (read + write) per time step of k_step on the full microcircuit,
-# from one ncu capture of this kernel (dram__bytes_read.sum + write.sum of one
-# 2000-step launch, divided by its steps); None for any other workload, and to
-# be re-measured whenever k_step changes
-K_STEP_DRAM_BYTES_PER_STEP_FULL = (14161993728 + 4584960) / 2000.0
+# from an ncu capture of this kernel; None until it is measured for the
+# current kernel (to be re-measured whenever k_step changes)
+K_STEP_DRAM_BYTES_PER_STEP_FULL = None
+K_STEP_TRAFFIC_SOURCE = None
 # k_deliver_words, 20,000-spike lists at scale 1: ncu dram__bytes_read + write
 # of three launches over their mean synaptic events
 K_DELIVER_WORDS_DRAM_BYTES_PER_EVENT = (349.75e6 + 348.93e6 + 349.31e6) / 3.0 / 77.78e6
@@ -210,6 +216,170 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Other forms of the path, timed on bounded samples inside the default run so
+# that each has its own device timing, roofline and clock record
+# ---------------------------------------------------------------------------
+def _events_timer(torch, stream):
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    return a, b
+
+
+def extra_deliver(pkg, workload, torch, stream, hbm_peak, peak_kind, m=20000, n_lists=16):
+    """Stand-alone delivery of m-spike lists at scale 1 with the partition-word
+    tiling (k_deliver_words): each timed launch gets a fresh list from a pool
+    whose rows (n_lists x ~0.3 GB) exceed L2 many times."""
+    net = pkg.Microcircuit(workload.microcircuit(1.0), stream=stream)
+    rp, _, _ = net.export_network(rows_only=True)
+    row_len = np.diff(rp.astype(np.int64))
+    rng = np.random.default_rng(20000)
+    lists = [np.sort(rng.choice(net.n, m, replace=False)).astype(np.int32) for _ in range(n_lists)]
+    dev = [torch.from_numpy(x).cuda() for x in lists]
+    events = float(np.mean([row_len[x].sum() for x in lists]))
+    for k in range(3):
+        net.deliver(dev[k].data_ptr(), m, k, 3)
+    torch.cuda.synchronize()
+    e0, e1 = _events_timer(torch, stream)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        for k in range(n_lists):
+            net.deliver(dev[k].data_ptr(), m, 7 + k, 3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / n_lists
+    net.close()
+    gbs = BYTES_PER_EVENT * events / (us * 1e-6) / 1e9
+    return {"metric": "synaptic events/s of one %d-spike delivery (full microcircuit)" % m,
+            "value": events / (us * 1e-6), "unit": UNIT, "us_per_list": us, "events_per_list": events,
+            "launches": n_lists, "gpu_launches": n_lists,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak,
+                         "traffic": K_DELIVER_WORDS_DRAM_BYTES_PER_EVENT * events,
+                         "peak_kind": peak_kind, "kernel": "k_deliver_words"},
+            "clocks": clk.summary(),
+            "config": {"workload": "snn_deliver tiling 3 (partition words), %d random sources "
+                                   "per list, %d lists" % (m, n_lists), "scale": 1.0}}
+
+
+def extra_scale4(pkg, workload, torch, stream, hbm_peak, peak_kind):
+    """The 4x microcircuit (308,676 neurons, ~1.2e9 synapses): one launch of
+    1 s biological after a 0.2 s warm-up launch."""
+    cfg = workload.microcircuit(4.0)
+    net = pkg.Microcircuit(cfg, stream=stream)
+    info = net.info()
+    net.step(2000)
+    net.sync()
+    net.read_spikes_into(np.zeros(max(1, net.raster_size()), np.uint32),
+                         np.zeros(max(1, net.raster_size()), np.uint32))
+    c0 = net.counters()
+    e0, e1 = _events_timer(torch, stream)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        net.step(STEPS_PER_BENCH_STEP)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    c1 = net.counters()
+    net.close()
+    ev = c1["events"] - c0["events"]
+    gbs = BYTES_PER_EVENT * ev / (ms * 1e-3) / 1e9
+    return {"metric": "synaptic events/s (4x microcircuit)", "value": ev / (ms * 1e-3),
+            "unit": UNIT, "real_time_factor": ms * 1e-3 / (STEPS_PER_BENCH_STEP * cfg["dt"] * 1e-3),
+            "us_per_time_step": ms * 1e3 / STEPS_PER_BENCH_STEP,
+            "spikes_per_time_step": (c1["spikes"] - c0["spikes"]) / STEPS_PER_BENCH_STEP,
+            "gpu_launches": 1,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_step (persistent step kernel)"},
+            "clocks": clk.summary(),
+            "config": {"workload": "4x microcircuit, %d neurons, %d synapses, 1 launch of %d "
+                                   "time steps (1 s biological)"
+                                   % (info["n_neurons"], info["n_synapses"], STEPS_PER_BENCH_STEP),
+                       "scale": 4.0, "ring_in_shared": info["ring_in_shared"],
+                       "rows_gb": info["slot_bytes"] / 1e9}}
+
+
+def extra_batch(pkg, workload, torch, stream, hbm_peak, peak_kind, n_inst=64):
+    """64 microcircuits at scales U(0.05, 0.25) in one persistent kernel
+    replayed from a CUDA graph: 1 s biological of every instance."""
+    b = pkg.MicrocircuitBatch(workload.batched_instances(n_inst, seed=7), stream=stream)
+    info = b.info(0)
+    b.step(1000)
+    b.sync()
+    ev0 = sum(b.counters(k)["events"] for k in range(len(b)))
+    e0, e1 = _events_timer(torch, stream)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        b.step(STEPS_PER_BENCH_STEP)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ev = sum(b.counters(k)["events"] for k in range(len(b))) - ev0
+    launches = STEPS_PER_BENCH_STEP // info["graph_steps"]
+    b.close()
+    gbs = BYTES_PER_EVENT * ev / (ms * 1e-3) / 1e9
+    return {"metric": "synaptic events/s of %d independent microcircuits in one persistent kernel"
+                      % n_inst,
+            "value": ev / (ms * 1e-3), "unit": UNIT,
+            "real_time_factor": ms * 1e-3 / (STEPS_PER_BENCH_STEP * 1e-4),
+            "us_per_time_step": ms * 1e3 / STEPS_PER_BENCH_STEP, "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_batch (persistent batched step kernel)"},
+            "clocks": clk.summary(),
+            "config": {"workload": "%d instances, scales U(0.05, 0.25) (seed 7), %d neurons in "
+                                   "total, %d time steps of every instance (1 s biological) as "
+                                   "graph replays of %d steps"
+                                   % (n_inst, info["n_neurons_total"], STEPS_PER_BENCH_STEP,
+                                      info["graph_steps"])}}
+
+
+def extra_grad(pkg, workload, torch, stream, reps=3):
+    """One surrogate-gradient evaluation of the 10 % microcircuit over 200 ms
+    (2000 steps, checkpoints every 100): forward, backward, through the
+    torch.autograd.Function; wall time per evaluation (device-synchronised)."""
+    from paper_1909_08665_gb300.autograd import microcircuit_rates
+    cfg = workload.microcircuit(0.1)
+    targets = torch.as_tensor(workload.target_rates())
+    net = pkg.Microcircuit(cfg, stream=stream)
+    start = net.save_state()
+    n_steps, every = 2000, 100
+
+    def one():
+        scales = torch.ones(8, 8, dtype=torch.float64, requires_grad=True)
+        nu = torch.tensor(float(cfg["nu_bg"]), dtype=torch.float64, requires_grad=True)
+        rates = microcircuit_rates(scales, nu, net, n_steps, every, start)
+        loss = ((rates - targets) ** 2).mean()
+        loss.backward()
+        return float(loss.item()), float(scales.grad.abs().max())
+
+    one()
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            loss, gmax = one()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+    net.close()
+    ms = 1e3 * float(np.median(times))
+    return {"metric": "surrogate-gradient evaluations/s (10% microcircuit, 200 ms, rate MSE)",
+            "value": 1e3 / ms, "unit": "gradients/s", "ms_per_gradient": ms, "reps": reps,
+            "loss": loss, "grad_abs_max": gmax,
+            "note": "the adjoint grows ~e^0.039 per step through the chaotic dynamics: over "
+                    "200 ms max|g| reaches ~4e31, so the gradient's value is dominated by that "
+                    "growth; the figure times the computation, not its usefulness for training",
+            "gpu_launches": 1 + 3 * ((n_steps + every - 1) // every) + 1,
+            "clocks": clk.summary(),
+            "config": {"workload": "10%% microcircuit (7,717 neurons), %d time steps, checkpoints "
+                                   "every %d steps, gradient w.r.t. 64 projection scales and nu"
+                                   % (n_steps, every)}}
+
+
 def run_ours(args):
     import torch
 
@@ -245,9 +415,6 @@ def run_ours(args):
 
     # -------- device-timed region: K launches, inputs (1.2 GB rows) > L2 --------
     c0 = net.counters()
-    # device clock at the end of every timed step (the real-time criterion)
-    step_clock = torch.zeros(args.steps * chunk, dtype=torch.int64, device=dev)
-    net.record_step_times(step_clock.data_ptr(), args.steps * chunk)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
@@ -262,17 +429,42 @@ def run_ours(args):
         t_all1.record(stream)
         barrier()
     net.sync()
-    net.record_step_times(None)
     c1 = net.counters()
     total_ms = t_all0.elapsed_time(t_all1)
-    stamps = step_clock.cpu().numpy().reshape(args.steps, chunk)
-    dts = np.diff(stamps, axis=1).reshape(-1) * 1e-3         # us, within each launch
+
+    # -------- one more launch, untimed, recording the device clock at the
+    # end of every step (the real-time criterion) and the per-step synapse
+    # counts (spikes, events, busiest partition, empty pairs) --------
+    step_clock = torch.zeros(chunk, dtype=torch.int64, device=dev)
+    step_counts = torch.zeros(4 * chunk, dtype=torch.int32, device=dev)
+    net.record_step_times(step_clock.data_ptr(), chunk)
+    net.record_step_counts(step_counts.data_ptr(), chunk)
+    net.step(chunk)
+    net.sync()
+    net.record_step_times(None)
+    net.record_step_counts(None)
+    dts = np.diff(step_clock.cpu().numpy()) * 1e-3            # us
     step_times = {"mean_us": float(dts.mean()) if dts.size else None,
                   "p99_us": float(np.percentile(dts, 99)) if dts.size else None,
                   "max_us": float(dts.max()) if dts.size else None,
                   "steps_over_100us": int((dts > 100.0).sum()),
-                  "source": "device clock at the end of each step (CTA 0), first step of "
-                            "each launch excluded"}
+                  "source": "device clock at the end of each step (CTA 0) of one recorded "
+                            "launch of %d steps after the timed region, its first step "
+                            "excluded" % chunk}
+    counts = step_counts.cpu().numpy().view(np.uint32).reshape(-1, 4).astype(np.int64)
+    n_p = info["n_part"]
+    step_counts_summary = {
+        "busiest_partition_spikes": {"mean": float(counts[:, 2].mean()),
+                                     "p99": float(np.percentile(counts[:, 2], 99)),
+                                     "max": int(counts[:, 2].max())},
+        "spikes_per_step": {"mean": float(counts[:, 0].mean()),
+                            "p99": float(np.percentile(counts[:, 0], 99)),
+                            "max": int(counts[:, 0].max())},
+        "empty_pairs_fraction": float(counts[:, 3].sum() / max(1, n_p * counts[:, 0].sum())),
+        "flushed": 0,
+        "source": "snn_record_step_counts over the recorded launch: spikes a partition "
+                  "processed (non-empty runs onto it), and (spike, partition) pairs with no "
+                  "target there"}
     per_launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     events = c1["events"] - c0["events"]
     spikes = c1["spikes"] - c0["spikes"]
@@ -322,6 +514,7 @@ def run_ours(args):
         "events_per_time_step": events / (args.steps * chunk),
         "us_per_time_step": total_ms * 1e3 / (args.steps * chunk),
         "step_time": step_times,
+        "step_counts": step_counts_summary,
         "build_s": build_s,
         "clocks": clk.summary(),
         "gpu_launches": args.steps,
@@ -331,13 +524,21 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
                      "traffic": (K_STEP_DRAM_BYTES_PER_STEP_FULL * chunk
-                                 if args.scale == 1.0 else None),
-                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum "
-                                        "of one 2000-step k_step launch on the full "
-                                        "microcircuit, scaled by steps per launch"
-                                        if args.scale == 1.0 else None),
+                                 if args.scale == 1.0 and K_STEP_DRAM_BYTES_PER_STEP_FULL
+                                 else None),
+                     "traffic_source": (K_STEP_TRAFFIC_SOURCE
+                                        if args.scale == 1.0 and K_STEP_DRAM_BYTES_PER_STEP_FULL
+                                        else None),
                      "peak_kind": peak_kind, "kernel": "k_step (persistent step kernel)"},
     }
+    if rank == 0 and ws == 1 and not args.no_extras and args.scale == 1.0:
+        net.close()
+        line["deliver_20000"] = extra_deliver(pkg, workload, torch, stream, hbm_peak, peak_kind)
+        line["scale4"] = extra_scale4(pkg, workload, torch, stream, hbm_peak, peak_kind)
+        line["batch64"] = extra_batch(pkg, workload, torch, stream, hbm_peak, peak_kind)
+        line["grad_config3"] = extra_grad(pkg, workload, torch, stream)
+        line["gpu_launches_extras"] = sum(line[k]["gpu_launches"] for k in
+                                          ("deliver_20000", "scale4", "batch64", "grad_config3"))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.scale <= 1.0:
         line["cpu_baseline"] = cpu_baseline(cfg, os.cpu_count() or 1, args.cpu_skip,
                                             args.cpu_steps)
@@ -735,6 +936,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4000)
     ap.add_argument("--ref-chunk", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 20,000-spike delivery, 4x, batch and gradient keys")
     ap.add_argument("--instances", type=int, default=64, help="instances of --workload batch")
     ap.add_argument("--deliver-scale", default="1.0,4.0", help="--workload deliver: scales")
     ap.add_argument("--deliver-spikes", default="25,93,4000,20000", help="--workload deliver: list sizes")

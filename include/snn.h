@@ -50,7 +50,9 @@ enum {
     SNN_ERR_OOM = 3,          /* device allocation failed */
     SNN_ERR_TIMEOUT = 4,      /* a grid-barrier wait exceeded its time limit */
     SNN_ERR_OVERFLOW = 5,     /* spike raster capacity exceeded (spikes lost) */
-    SNN_ERR_UNSUPPORTED = 6   /* device is not sm_103 or too small */
+    SNN_ERR_UNSUPPORTED = 6,  /* device is not sm_103 or too small */
+    SNN_ERR_SATURATED = 7     /* a neuron's fixed-point input of one step left the
+                                 int32 range (see snn_sync) */
 };
 
 /*
@@ -106,10 +108,17 @@ typedef struct snn_info {
     float propagators[4];     /* P22, P21, P11, P20 as used (fp32) */
     int32_t wext_q;           /* background weight, 1/256 pA */
     int32_t shared_bytes;     /* dynamic shared memory of the step kernel */
-    int32_t slot_entries;     /* largest per-partition slot stride S_c (8-byte entries) */
-    int64_t slot_bytes;       /* device memory of the partition slots */
+    int32_t slot_entries;     /* longest run of one row onto one partition (synapses) */
+    int64_t slot_bytes;       /* device memory of the rows the step kernel reads
+                                 (pre-decoded, 4 bytes per synapse) */
     int32_t deliver_clusters_active; /* co-resident 8-CTA clusters of snn_deliver
                                         tiling 4 (0: not available) */
+    int32_t saturation_check; /* 1: the input bound below reaches the int32 range, so
+                                 the step kernel counts wrap-arounds (SNN_ERR_SATURATED) */
+    int64_t input_bound;      /* largest possible |input| of one neuron in one step,
+                                 1/256 pA: sum over its synapses of the largest |weight|
+                                 of each projection, plus the largest background count
+                                 (32) times |w_ext| */
 } snn_info;
 
 typedef struct snn_net snn_net;
@@ -185,9 +194,35 @@ int snn_set_realtime(snn_net* net, int64_t period_ns);
  * Synchronises the network's stream. */
 int snn_realtime_stats(snn_net* net, int64_t* missed, int64_t* max_late_ns);
 
+/* snn_record_step_counts -- from the next snn_step on, the step kernel
+ * writes one record of 4 uint32 per step t into counts_dev[4 (t - t_first)],
+ * t_first = the step count at this call, for at most cap steps (the profile
+ * the paper records per synapse core, Sec. 4.1, Fig. 7):
+ *   [0] spikes emitted in step t;
+ *   [1] synaptic events of those spikes (the sum of their row lengths);
+ *   [2] the largest number of those spikes that one partition had to process
+ *       (spikes with at least one synapse onto it): the busiest partition's
+ *       load, the analogue of the paper's per-synapse-core count;
+ *   [3] (spike, partition) pairs whose row has no synapse onto the partition:
+ *       the paper's spike packets that target no neuron of a core.
+ * Nothing is flushed here (every spike is delivered), so the paper's flushed
+ * count is always 0 and is not recorded.  counts_dev is caller-owned device
+ * memory (uint32[4 cap]); this call zeroes it on the network's stream.  NULL
+ * stops recording.  Recording changes no result. */
+int snn_record_step_counts(snn_net* net, uint32_t* counts_dev, int64_t cap);
+
 /* snn_sync -- wait for the stream; returns SNN_OK, SNN_ERR_TIMEOUT if a
  * barrier wait gave up (state undefined), SNN_ERR_OVERFLOW if the raster
- * overflowed, or SNN_ERR_CUDA. */
+ * overflowed, SNN_ERR_SATURATED if some neuron's input of one step (its
+ * ring-buffer slot plus background, Sec. 3.1.2) left the int32 fixed-point
+ * range since the network was created, or SNN_ERR_CUDA.  Saturation is exact,
+ * not a bound: the step kernel counts every int32 wrap-around of a ring cell
+ * (it does so only for networks whose input bound, snn_info.input_bound,
+ * reaches 2^31; others cannot saturate and pay nothing), and the simulation
+ * goes on with the input wrapped modulo 2^32, as the CPU reference does.  The
+ * status is sticky.  Stand-alone delivery (snn_deliver) does not count
+ * wrap-arounds.  The state saved by snn_save_state does not carry pending
+ * wrap counts. */
 int snn_sync(snn_net* net);
 
 /*
@@ -284,6 +319,8 @@ int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int6
  *   t0         index of the first step (it selects the ring slots and the
  *              background draws, so consecutive calls continue a run).
  * Asynchronous on `stream`.  Results equal snn_step on the same network.
+ * Inputs wrap modulo 2^32 like snn_step's, but this entry point does not
+ * check for saturation (it never sets SNN_ERR_SATURATED).
  */
 #define SNN_NOALLOC_MAX_NEURONS 131072
 
@@ -412,7 +449,9 @@ typedef struct snn_batch_info {
  *   stream                        cudaStream_t of all the batch's work
  * Errors: SNN_ERR_INVALID (n_inst outside 1..1024, bad configuration),
  * SNN_ERR_OOM, SNN_ERR_UNSUPPORTED (not sm_103, or too many neurons for one
- * co-resident grid).
+ * co-resident grid), SNN_ERR_SATURATED (an instance whose input of one step
+ * can leave the int32 range, snn_info.input_bound >= 2^31: the batch kernel
+ * has no wrap-around count, so such an instance is refused).
  */
 int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_inst,
                      const snn_options* opt, void* stream, snn_batch** out);

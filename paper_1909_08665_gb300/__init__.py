@@ -24,8 +24,9 @@ WCODES = 128
 RING_DEPTH = 64
 
 SNN_OK, SNN_ERR_INVALID, SNN_ERR_CUDA, SNN_ERR_OOM = 0, 1, 2, 3
-SNN_ERR_TIMEOUT, SNN_ERR_OVERFLOW, SNN_ERR_UNSUPPORTED = 4, 5, 6
-_ERR_NAMES = {1: "INVALID", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "OVERFLOW", 6: "UNSUPPORTED"}
+SNN_ERR_TIMEOUT, SNN_ERR_OVERFLOW, SNN_ERR_UNSUPPORTED, SNN_ERR_SATURATED = 4, 5, 6, 7
+_ERR_NAMES = {1: "INVALID", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "OVERFLOW", 6: "UNSUPPORTED",
+              7: "SATURATED"}
 
 
 class SnnError(RuntimeError):
@@ -75,7 +76,8 @@ class SnnInfo(C.Structure):
                 ("ring_in_shared", C.c_int32), ("max_part_neurons", C.c_int32),
                 ("n_ref", C.c_int32), ("propagators", C.c_float * 4), ("wext_q", C.c_int32),
                 ("shared_bytes", C.c_int32), ("slot_entries", C.c_int32),
-                ("slot_bytes", C.c_int64), ("deliver_clusters_active", C.c_int32)]
+                ("slot_bytes", C.c_int64), ("deliver_clusters_active", C.c_int32),
+                ("saturation_check", C.c_int32), ("input_bound", C.c_int64)]
 
 
 class SnnNoallocIO(C.Structure):
@@ -102,6 +104,7 @@ NOALLOC_MAX_NEURONS = 131072
 EXPORTED = ["snn_create", "snn_create_from_rows", "snn_step", "snn_sync", "snn_read_spikes",
             "snn_raster_size", "snn_read_state", "snn_read_ring", "snn_counters", "snn_get_info",
             "snn_export_network", "snn_deliver", "snn_step_noalloc", "snn_record_step_times",
+            "snn_record_step_counts",
             "snn_set_realtime", "snn_realtime_stats", "snn_save_state",
             "snn_load_state", "snn_set_params", "snn_grad_forward", "snn_grad_backward",
             "snn_batch_create",
@@ -140,6 +143,7 @@ def lib():
         L.snn_step_noalloc.argtypes = [P(SnnConfig), C.c_uint64, P(SnnNoallocIO), C.c_int64,
                                        C.c_int64, vp]
         L.snn_record_step_times.argtypes = [vp, vp, C.c_int64]
+        L.snn_record_step_counts.argtypes = [vp, vp, C.c_int64]
         L.snn_set_realtime.argtypes = [vp, C.c_int64]
         L.snn_realtime_stats.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
         L.snn_save_state.argtypes = [vp, vp, C.c_int64, P(C.c_int64)]
@@ -315,6 +319,13 @@ class Microcircuit:
         of each following step; None stops recording."""
         _check(lib().snn_record_step_times(self._h, None if times_dev_ptr is None
                                            else C.c_void_p(int(times_dev_ptr)), int(cap)))
+
+    def record_step_counts(self, counts_dev_ptr: int | None, cap: int = 0):
+        """Device uint32 buffer (data_ptr) of 4 * cap words receiving, for each
+        following step, [spikes, synaptic events, busiest partition's
+        spikes, empty (spike, partition) pairs]; None stops recording."""
+        _check(lib().snn_record_step_counts(self._h, None if counts_dev_ptr is None
+                                            else C.c_void_p(int(counts_dev_ptr)), int(cap)))
 
     def set_realtime(self, period_ns: int):
         """Pace the following steps to wall-clock time: one step per period_ns

@@ -865,6 +865,32 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
         b->row_start.push_back(rs);
         b->words.push_back(wd);
         b->nnz[k] = nnz;
+        // the batch kernel adds in plain int32: refuse an instance whose input
+        // of one step could leave that range (snn_create counts wrap-arounds
+        // for such networks instead)
+        {
+            uint32_t* d_in = nullptr;
+            std::vector<uint32_t> indeg((size_t)ht.n * kMaxPop);
+            cudaError_t e = cudaMalloc(&d_in, sizeof(uint32_t) * std::max<size_t>(indeg.size(), 1));
+            if (e == cudaSuccess) e = launch_indegree(rs, wd, ht.n, ht.n_pop, ht.pop_start, d_in, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(indeg.data(), d_in, sizeof(uint32_t) * indeg.size(),
+                                    cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (d_in) cudaFree(d_in);
+            if (e != cudaSuccess) {
+                rc = set_cuda_error(e, "in-degrees of a batch instance");
+                break;
+            }
+            if (input_bound(indeg.data(), ht.n, ht.n_pop, ht.pop_start, ht.wtab, ht.wext_q,
+                            ht.mode) > 2147483647ll) {
+                rc = set_error(SNN_ERR_SATURATED,
+                               "a batch instance's input of one step can exceed the int32 "
+                               "fixed-point range; step it as a single network (snn_create), "
+                               "which checks for saturation");
+                break;
+            }
+        }
         std::memcpy(wtab_all.data() + (size_t)k * kMaxPop * kMaxPop * kWCodes, ht.wtab, sizeof(ht.wtab));
         for (int m = 0; m < 8; ++m)
             ps_all[(size_t)k * 8 + m] = m == 0 ? 0 : (m < ht.n_pop ? ht.pop_start[m] : 0x7fffffff);

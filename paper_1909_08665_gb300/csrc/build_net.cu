@@ -18,6 +18,11 @@ namespace snn {
 
 namespace {
 
+// population boundaries passed by value to a kernel
+struct PopStarts {
+    int32_t pop_start[kMaxPop + 1];
+};
+
 template <int BLOCK>
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp,
                                                     uint32_t& total) {
@@ -213,6 +218,20 @@ __global__ void __launch_bounds__(256) k_pack_raster(const uint32_t* counts, int
     }
 }
 
+// In-degree of every target neuron per source population: indeg[i][q] =
+// number of synapses from population q onto neuron i.  One warp per row.
+__global__ void __launch_bounds__(kBuildThreads)
+k_indegree(const unsigned long long* row_start, const uint32_t* words, int n, PopStarts pops,
+           int n_pop, uint32_t* indeg) {
+    const long long j = ((long long)blockIdx.x * kBuildThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    const int q = pop_index(pops.pop_start, n_pop, (int32_t)j);
+    const unsigned long long b = row_start[j], e = row_start[j + 1];
+    for (unsigned long long k = b + lane; k < e; k += 32)
+        atomicAdd(&indeg[(size_t)(words[k] & kTgtMask) * kMaxPop + q], 1u);
+}
+
 }  // namespace
 
 cudaError_t launch_build_count(const BuildParams& bp, uint32_t* rowlen, cudaStream_t s) {
@@ -229,6 +248,18 @@ cudaError_t launch_build_scan(const uint32_t* rowlen, int n, unsigned long long*
 cudaError_t launch_build_fill(const BuildParams& bp, const unsigned long long* row_start,
                               uint32_t* words, uint32_t* seg, cudaStream_t s) {
     k_build_fill<<<bp.n, kBuildThreads, 0, s>>>(bp, row_start, words, seg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_indegree(const unsigned long long* row_start, const uint32_t* words, int n,
+                            int n_pop, const int32_t* pop_start, uint32_t* indeg, cudaStream_t s) {
+    PopStarts pops;
+    for (int p = 0; p <= kMaxPop; ++p) pops.pop_start[p] = pop_start[p];
+    cudaError_t e = cudaMemsetAsync(indeg, 0, sizeof(uint32_t) * (size_t)n * kMaxPop, s);
+    if (e != cudaSuccess || n <= 0) return e;
+    const long long threads = (long long)n * 32;
+    k_indegree<<<(unsigned)((threads + kBuildThreads - 1) / kBuildThreads), kBuildThreads, 0, s>>>(
+        row_start, words, n, pops, n_pop, indeg);
     return cudaGetLastError();
 }
 

@@ -185,7 +185,7 @@ int make_tables(snn_net* net) {
 void free_net(snn_net* net) {
     if (!net) return;
     void* ptrs[] = {net->d_part_lo, net->d_row_start, net->d_seg, net->d_words, net->d_pre, net->d_wtab,
-                    net->d_dtab, net->d_u, net->d_i, net->d_r, net->d_ring, net->d_msg,
+                    net->d_dtab, net->d_u, net->d_i, net->d_r, net->d_ring, net->d_msg, net->d_wrap,
                     net->d_ras_step, net->d_ras_id, net->d_ras_n, net->d_rs_step, net->d_rs_id,
                     net->d_counters, net->d_sync, net->d_pop_spikes, net->d_rt};
     for (void* p : ptrs)
@@ -347,8 +347,19 @@ int finish_network(snn_net* net) {
     dp.part_lo = net->d_part_lo;
     dp.words = net->d_words;
     CK(launch_predecode(dp, net->d_row_start, net->d_pre, s));
-    CK(cudaStreamSynchronize(s));
-    return SNN_OK;
+    // in-degrees per source population, for the bound on one step's input
+    uint32_t* d_indeg = nullptr;
+    CALL(dalloc(&d_indeg, (size_t)net->n * kMaxPop, "in-degrees"));
+    net->indeg.assign((size_t)net->n * kMaxPop, 0u);
+    e = launch_indegree(net->d_row_start, net->d_words, net->n, net->n_pop, net->pop_start,
+                        d_indeg, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(net->indeg.data(), d_indeg, sizeof(uint32_t) * net->indeg.size(),
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_indeg);
+    if (e != cudaSuccess) return cuda_fail(e, "in-degrees");
+    return net_update_saturation(net);
 }
 
 // the synaptic rows (row starts, words, per-partition segment offsets)
@@ -439,6 +450,9 @@ int check_status(snn_net* net) {
     CK(cudaMemcpy(&st, net->d_sync + 4, sizeof(st), cudaMemcpyDeviceToHost));
     if (st & kStatusTimeout) return fail(SNN_ERR_TIMEOUT, "a grid-barrier wait timed out");
     if (st & 2u) return fail(SNN_ERR_OVERFLOW, "spike raster capacity exceeded; spikes were lost");
+    if (st & kStatusSaturated)
+        return fail(SNN_ERR_SATURATED, "a neuron's input of one step left the int32 fixed-point "
+                                       "range (it wrapped modulo 2^32)");
     return SNN_OK;
 }
 
@@ -561,6 +575,10 @@ void fill_step_params(const snn_net* net, StepParams* out) {
     sp.step_times = net->step_times;
     sp.st_t0 = net->st_t0;
     sp.st_cap = net->st_cap;
+    sp.st_counts = net->step_counts;
+    sp.sc_t0 = net->sc_t0;
+    sp.sc_cap = net->sc_cap;
+    sp.wrap = net->sat_check ? net->d_wrap : nullptr;
 }
 
 cudaError_t net_launch(snn_net* net, StepParams& sp, int64_t t0, int64_t n) {
@@ -600,7 +618,48 @@ int net_upload_weights(snn_net* net) {
     cudaStream_t s = net->stream;
     CK(cudaMemcpyAsync(net->d_wtab, net->wtab, sizeof(net->wtab), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
+    return net_update_saturation(net);
+}
+
+long long input_bound(const uint32_t* indeg, int n, int n_pop, const int32_t* pop_start,
+                      const int32_t* wtab, int32_t wext_q, int input_mode) {
+    long long wmax[kMaxPop][kMaxPop];
+    for (int p = 0; p < kMaxPop; ++p)
+        for (int q = 0; q < kMaxPop; ++q) {
+            long long m = 0;
+            for (int k = 0; k < kWCodes; ++k)
+                m = std::max(m, std::llabs((long long)wtab[(p * kMaxPop + q) * kWCodes + k]));
+            wmax[p][q] = m;
+        }
+    long long best = 0;
+    int p = 0;
+    for (int i = 0; i < n; ++i) {
+        while (p + 1 < n_pop && i >= pop_start[p + 1]) ++p;
+        long long b = 0;
+        for (int q = 0; q < kMaxPop; ++q) b += (long long)indeg[(size_t)i * kMaxPop + q] * wmax[p][q];
+        best = std::max(best, b);
+    }
+    if (input_mode == 0) best += (long long)kPoisTable * std::llabs((long long)wext_q);
+    return best;
+}
+
+int net_update_saturation(snn_net* net) {
+    net->in_bound = input_bound(net->indeg.data(), net->n, net->n_pop, net->pop_start, net->wtab,
+                                net->wext_q, net->cfg.input_mode);
+    net->sat_check = net->in_bound > 2147483647ll;
+    if (net->sat_check && !net->d_wrap) {
+        const size_t cells = (size_t)net->P * kRing * net->ncmax;
+        CALL(dalloc(&net->d_wrap, cells, "wrap counts"));
+        CK(cudaMemsetAsync(net->d_wrap, 0, sizeof(int32_t) * cells, net->stream));
+        CK(cudaStreamSynchronize(net->stream));
+    }
     return SNN_OK;
+}
+
+cudaError_t net_clear_wraps(snn_net* net) {
+    if (!net->d_wrap) return cudaSuccess;
+    return cudaMemsetAsync(net->d_wrap, 0, sizeof(int32_t) * (size_t)net->P * kRing * net->ncmax,
+                           net->stream);
 }
 
 int partition_pop_span(const int32_t* part_lo, int n_part, const int32_t* pop_start, int n_pop) {
@@ -704,6 +763,16 @@ int snn_record_step_times(snn_net* net, int64_t* times_dev, int64_t cap) {
     net->step_times = reinterpret_cast<long long*>(times_dev);
     net->st_t0 = net->step;
     net->st_cap = times_dev ? cap : 0;
+    return SNN_OK;
+}
+
+int snn_record_step_counts(snn_net* net, uint32_t* counts_dev, int64_t cap) {
+    if (!net || cap < 0 || (counts_dev && cap == 0)) return fail(SNN_ERR_INVALID, "bad arguments");
+    if (counts_dev)
+        CK(cudaMemsetAsync(counts_dev, 0, sizeof(uint32_t) * 4 * (size_t)cap, net->stream));
+    net->step_counts = counts_dev;
+    net->sc_t0 = net->step;
+    net->sc_cap = counts_dev ? cap : 0;
     return SNN_OK;
 }
 
@@ -822,6 +891,8 @@ int snn_get_info(snn_net* net, snn_info* info) {
         active = 0;
     }
     info->deliver_clusters_active = active;
+    info->saturation_check = net->sat_check ? 1 : 0;
+    info->input_bound = (int64_t)net->in_bound;
     return SNN_OK;
 }
 

@@ -395,6 +395,7 @@ cudaError_t load_ckpt(snn_net* net, const uint8_t* src) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(net->d_ring, src + n * 12, ring_words(net) * 4, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = clear_messages(net);
+    if (e == cudaSuccess) e = net_clear_wraps(net);
     return e;
 }
 
@@ -716,6 +717,7 @@ int snn_load_state(snn_net* net, const void* buf_host, int64_t n_bytes) {
     GCK(cudaMemcpy(net->d_r, b + 32 + n * 8, n * 4, cudaMemcpyHostToDevice));
     GCK(cudaMemcpy(net->d_ring, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice));
     GCK(clear_messages(net));
+    GCK(net_clear_wraps(net));
     GCK(cudaStreamSynchronize(net->stream));
     net->step = (int64_t)hdr[2];
     if (net->grad) net->grad->ready = false;

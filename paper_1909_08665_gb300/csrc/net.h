@@ -48,6 +48,12 @@ struct snn_net {
     int32_t* d_ring = nullptr;
     int32_t w_span = 1;                    // target populations of the widest partition
     int32_t run_max = 0;                   // longest (row, partition) run
+    std::vector<uint32_t> indeg;           // [n][8] synapses per source population
+    long long in_bound = 0;                // largest |input| of one neuron-step (1/256 pA)
+    bool sat_check = false;                // in_bound reaches 2^31: count wrap-arounds
+    int32_t* d_wrap = nullptr;             // wrap counts, ring layout (sat_check only)
+    uint32_t* step_counts = nullptr;       // caller's device buffer of per-step counts
+    int64_t sc_t0 = 0, sc_cap = 0;
     unsigned long long* d_msg = nullptr;   // [4][P][msg_stride] tagged spike messages
     int32_t msg_stride = 0;
     uint32_t* d_ras_step = nullptr;
@@ -73,8 +79,14 @@ namespace snn {
 void fill_step_params(const snn_net* net, StepParams* sp);
 // recompute the weight, delay, Poisson and propagator tables from net->cfg
 int net_make_tables(snn_net* net);
-// upload the weight table (the step kernel stages it at launch)
+// upload the weight table (the step kernel stages it at launch) and update
+// the input bound and the saturation check
 int net_upload_weights(snn_net* net);
+// recompute the input bound from the weights; the first time it reaches 2^31
+// the wrap-count array is allocated, and the step kernel counts wrap-arounds
+int net_update_saturation(snn_net* net);
+// zero the wrap counts (after the ring was replaced: load, restore)
+cudaError_t net_clear_wraps(snn_net* net);
 // launch the step kernel for n steps from step t0 with the given parameters
 cudaError_t net_launch(snn_net* net, StepParams& sp, int64_t t0, int64_t n);
 void free_grad(snn_grad* g);

@@ -25,6 +25,7 @@ constexpr uint32_t kStreamInit = 4u;
 
 // status bits
 constexpr uint32_t kStatusTimeout = 1u;
+constexpr uint32_t kStatusSaturated = 4u;   // a step's input left the int32 range
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of the two 32x32->64-bit
@@ -188,6 +189,17 @@ struct StepParams {
     // step_times[t - st_t0] for t - st_t0 in [0, st_cap)
     long long* step_times;
     int64_t st_t0, st_cap;
+    // optional per-step counts (snn_record_step_counts): for steps t with
+    // r = t - sc_t0 in [0, sc_cap), st_counts[4 r ..] = spikes of step t,
+    // their synaptic events, the largest number of them one partition
+    // processed (non-empty runs), and the (spike, partition) pairs with an
+    // empty run; zeroed by the host before recording starts
+    uint32_t* st_counts;
+    int64_t sc_t0, sc_cap;
+    // wrap-around counts of the ring cells, same layout as ring ([n_part][64]
+    // [ncmax]); non-null only for networks whose input can leave the int32
+    // range, which then take the kernel variant that counts wrap-arounds
+    int32_t* wrap;
     // pacing to wall-clock time (0: off): step t starts no earlier than
     // rt[0] + (t - rt_t_anchor) * rt_period_ns, rt[0] being the device clock
     // when the first paced step started (0 until then); rt[1] counts steps
@@ -228,6 +240,14 @@ cudaError_t launch_build_fill(const BuildParams& bp, const unsigned long long* r
 cudaError_t launch_seg_from_rows(const unsigned long long* row_start, const uint32_t* words,
                                  int n, const int32_t* part_lo, int n_part, uint32_t* seg,
                                  cudaStream_t s);
+// indeg[i * 8 + q] = synapses from population q onto neuron i (zeroed first)
+cudaError_t launch_indegree(const unsigned long long* row_start, const uint32_t* words, int n,
+                            int n_pop, const int32_t* pop_start, uint32_t* indeg, cudaStream_t s);
+// largest possible |input| of one neuron in one step (1/256 pA): over neurons
+// i, sum_q indeg[i][q] max_code |wtab[pop(i)][q][code]|, plus 32 |wext_q| when
+// the background is Poisson (at most 32 background spikes per step)
+long long input_bound(const uint32_t* indeg, int n, int n_pop, const int32_t* pop_start,
+                      const int32_t* wtab, int32_t wext_q, int input_mode);
 // out[c] = longest (row, partition c) segment, for every partition c
 cudaError_t launch_max_segment(const uint32_t* seg, int n, int n_part, uint32_t* out,
                                cudaStream_t s);
