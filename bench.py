@@ -58,14 +58,20 @@ METRIC = "real-time factor and synaptic events/s (full microcircuit, 1 GB300); %
 UNIT = "synaptic events/s"
 STEPS_PER_BENCH_STEP = 10000          # 1 s of biological time at dt = 0.1 ms
 BYTES_PER_EVENT = 4                   # one packed synaptic word read per event
-# DRAM bytes (read + write) per time step of k_step on the full microcircuit,
-# from an ncu capture of this kernel; None until it is measured for the
-# current kernel (to be re-measured whenever k_step changes)
-K_STEP_DRAM_BYTES_PER_STEP_FULL = None
-K_STEP_TRAFFIC_SOURCE = None
-# k_deliver_words, 20,000-spike lists at scale 1: ncu dram__bytes_read + write
-# of three launches over their mean synaptic events
-K_DELIVER_WORDS_DRAM_BYTES_PER_EVENT = (349.75e6 + 348.93e6 + 349.31e6) / 3.0 / 77.78e6
+# DRAM bytes (read + write) per synaptic event of k_step, from one ncu capture
+# of the current kernel on the small case (scale 0.4: dram__bytes_read.sum +
+# dram__bytes_write.sum of one 2000-step launch that delivered 19,040.77
+# events per step); the full-size launch's traffic is taken as this figure
+# times its events (re-measure whenever k_step changes)
+K_STEP_DRAM_BYTES_PER_EVENT = (108.061184e6 + 3.393792e6) / (2000 * 19040.7745)
+K_STEP_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 2000-step "
+                         "k_step launch at scale 0.4 (30,868 neurons, 192 MB of rows): 2.93 B "
+                         "per synaptic event, times this launch's events; a lower estimate at "
+                         "full size, where fewer rows stay L2-resident between spikes")
+# k_deliver_words, 20,000-spike lists on the small case (scale 0.4): ncu
+# dram__bytes_read + write of three launches over their mean synaptic events
+K_DELIVER_WORDS_DRAM_BYTES_PER_EVENT = ((138.634752 + 138.895360 + 139.256832) +
+                                        (3.372800 + 3.639808 + 3.398656)) * 1e6 / 3.0 / 31.06e6
 
 
 def load_peaks():
@@ -502,7 +508,8 @@ def run_ours(args):
         "config": {"workload": "%s, %d LIF neurons, %d synapses, Poisson background, dt 0.1 "
                                "ms; 1 step = %d time steps (%g s biological)"
                                % ("full microcircuit" if args.scale == 1.0
-                                  else "%gx microcircuit (same in-degrees)" % args.scale,
+                                  else "%gx microcircuit%s" % (args.scale, " (same in-degrees)"
+                                                               if args.scale > 1.0 else ""),
                                   info["n_neurons"], info["n_synapses"], chunk, chunk * 1e-4),
                    "scale": args.scale, "seed": cfg["seed"], "time_steps_per_step": chunk,
                    "l2": "no flush: synapse rows (%.2f GB) exceed the 129 MB L2"
@@ -523,12 +530,9 @@ def run_ours(args):
                 "real_time_factor": e2e_s / bio_s},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
-                     "traffic": (K_STEP_DRAM_BYTES_PER_STEP_FULL * chunk
-                                 if args.scale == 1.0 and K_STEP_DRAM_BYTES_PER_STEP_FULL
-                                 else None),
-                     "traffic_source": (K_STEP_TRAFFIC_SOURCE
-                                        if args.scale == 1.0 and K_STEP_DRAM_BYTES_PER_STEP_FULL
-                                        else None),
+                     "traffic": (K_STEP_DRAM_BYTES_PER_EVENT * events / args.steps
+                                 if args.scale == 1.0 else None),
+                     "traffic_source": K_STEP_TRAFFIC_SOURCE if args.scale == 1.0 else None,
                      "peak_kind": peak_kind, "kernel": "k_step (persistent step kernel)"},
     }
     if rank == 0 and ws == 1 and not args.no_extras and args.scale == 1.0:
