@@ -568,3 +568,37 @@ def binned_correlations(steps, ids, neuron_ids, t_start: int, t_stop: int, bin_s
     cc = np.corrcoef(mat)
     iu = np.triu_indices(mat.shape[0], 1)
     return cc[iu]
+
+
+def population_statistics(cfg: dict, steps, ids, t_start: int, t_stop: int,
+                          n_corr: int = 200) -> dict:
+    """The within-population statistics the paper compares between
+    simulators (Sec. 4.2) over steps [t_start, t_stop): per population, the
+    mean and standard deviation of single-neuron firing rates (Hz), the mean
+    coefficient of variation of inter-spike intervals (neurons with at least 3
+    spikes), and the mean correlation coefficient between the binned spike
+    trains of its first ``n_corr`` neurons.  Spike trains are binned by the
+    Freedman-Diaconis rule applied to the population's pooled spike times in
+    the window."""
+    steps = np.asarray(steps, np.int64)
+    ids = np.asarray(ids, np.int64)
+    n = int(sum(cfg["pop_sizes"]))
+    bounds = np.cumsum([0] + list(cfg["pop_sizes"]))
+    rates = neuron_rates(cfg, steps, ids, t_start, t_stop)
+    cv = cv_isi(steps, ids, n, t_start, t_stop)
+    win = (steps >= t_start) & (steps < t_stop)
+    out = {"rate_mean": [], "rate_sd": [], "cv_mean": [], "corr_mean": [], "corr_bin_steps": []}
+    for p in range(len(cfg["pop_sizes"])):
+        lo, hi = int(bounds[p]), int(bounds[p + 1])
+        out["rate_mean"].append(float(rates[lo:hi].mean()))
+        out["rate_sd"].append(float(rates[lo:hi].std()))
+        c = cv[lo:hi]
+        out["cv_mean"].append(float(np.nanmean(c)) if np.isfinite(c).any() else float("nan"))
+        pooled = steps[win & (ids >= lo) & (ids < hi)]
+        width = max(1, int(round(freedman_diaconis_width(pooled)))) if pooled.size > 1 else 1
+        cc = binned_correlations(steps, ids, np.arange(lo, min(lo + n_corr, hi)), t_start, t_stop,
+                                 width)
+        out["corr_mean"].append(float(np.mean(cc)) if cc.size else 0.0)
+        out["corr_bin_steps"].append(width)
+    return out
+

@@ -52,6 +52,7 @@ constexpr int kWarps = kStepThreads / 32;
 constexpr uint32_t kStatusRasterOverflow = 2u;
 constexpr int kInline = 7;              // ids read together with a message header (64 B)
 constexpr int kRunWave = 4;             // run entries per lane loaded at once (128 per spike)
+constexpr int kBatchSpikes = 4;         // spikes a warp takes at once
 constexpr uint32_t kPopWords = kMaxPop * kWCodes;   // weight-table entries per target population
 
 // ---------------------------------------------------------------------------
@@ -147,12 +148,12 @@ __device__ inline bool poll_word(const StepParams& sp, const unsigned long long*
 
 // ---------------------------------------------------------------------------
 // the runs s_rb/s_rl[0, m) of the spikes of step tb into this CTA's ring:
-// batches of 4 spikes per warp.  Entry x of a run (a pre-decoded synapse) is
+// batches of kBatchSpikes spikes per warp.  Entry x of a run (a pre-decoded synapse) is
 // the weight-table index x >> kPreOffBits and the ring offset
 // x & kPreOffMask = delay * ncmax + local target; its weight, looked up in
 // s_w (table rows from population p_lo on, wbase = p_lo * kPopWords), is
 // added at ((tb mod 64) * ncmax + offset) wrapped into the 64-slot ring.  Each
-// lane loads entries lane + 32 h (h < kRunWave) of all 4 runs before the
+// lane loads entries lane + 32 h (h < kRunWave) of all the batch's runs before the
 // first add (all loads in flight at once); longer runs finish in a loop.
 // ---------------------------------------------------------------------------
 // SAT: the networks whose input can leave the int32 range also count, per
@@ -188,11 +189,11 @@ __device__ __forceinline__ void deliver_batches(const StepParams& sp, const uint
     const int32_t R = kRing * sp.ncmax;                  // ring words of this CTA
     const int32_t base_t = (int32_t)(((uint32_t)tb & (kRing - 1)) * (uint32_t)sp.ncmax);
     const uint32_t* pre = sp.pre;
-    for (uint32_t g0 = (uint32_t)warp * 4u; g0 < m; g0 += (uint32_t)kWarps * 4u) {
-        uint32_t rb[4], rl[4];
-        uint32_t ev[4][kRunWave];
+    for (uint32_t g0 = (uint32_t)warp * kBatchSpikes; g0 < m; g0 += (uint32_t)kWarps * kBatchSpikes) {
+        uint32_t rb[kBatchSpikes], rl[kBatchSpikes];
+        uint32_t ev[kBatchSpikes][kRunWave];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kBatchSpikes; ++k) {
             const bool ok = g0 + (uint32_t)k < m;
             rb[k] = ok ? s_rb[g0 + k] : 0u;
             rl[k] = ok ? s_rl[g0 + k] : 0u;
@@ -203,7 +204,7 @@ __device__ __forceinline__ void deliver_batches(const StepParams& sp, const uint
             }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kBatchSpikes; ++k) {
 #pragma unroll
             for (int h = 0; h < kRunWave; ++h)
                 if ((uint32_t)lane + 32u * (uint32_t)h < rl[k])
@@ -214,8 +215,12 @@ __device__ __forceinline__ void deliver_batches(const StepParams& sp, const uint
             if (lane == 0) events += rl[k];
         }
         if (s_cnt != nullptr && lane == 0) {
-            const uint32_t ev_sum = rl[0] + rl[1] + rl[2] + rl[3];
-            const uint32_t busy = (rl[0] > 0u) + (rl[1] > 0u) + (rl[2] > 0u) + (rl[3] > 0u);
+            uint32_t ev_sum = 0u, busy = 0u;
+#pragma unroll
+            for (int k = 0; k < kBatchSpikes; ++k) {
+                ev_sum += rl[k];
+                busy += rl[k] > 0u ? 1u : 0u;
+            }
             atomicAdd(&s_cnt[0], ev_sum);
             atomicAdd(&s_cnt[1], busy);
         }
