@@ -25,8 +25,8 @@
 //         its own tag, so a matching tag is both the grid-wide barrier and
 //         the data; no fence, no counter), look up each spike's run for this
 //         partition and deliver those spikes into ring slots t-1+d (d >= 1):
-//         per warp, batches of 4 spikes whose runs are all loaded before the
-//         shared-memory atomics.
+//         per warp, batches of kBatchSpikes spikes whose runs are all loaded
+//         before the shared-memory atomics.
 //   C(t)  acc = ring[t] (cleared) + background; I_t = P11 I_{t-1} + acc/256.
 // A(t+1) needs only I_t, and the spikes of step t reach no input before
 // slot t+1, so the spike exchange of one step overlaps the next step's
@@ -51,8 +51,13 @@ namespace snn {
 constexpr int kWarps = kStepThreads / 32;
 constexpr uint32_t kStatusRasterOverflow = 2u;
 constexpr int kInline = 7;              // ids read together with a message header (64 B)
-constexpr int kRunWave = 4;             // run entries per lane loaded at once (128 per spike)
-constexpr int kBatchSpikes = 4;         // spikes a warp takes at once
+// a warp takes kBatchSpikes spikes at once and loads the first 32 kRunWave
+// entries of each of their runs in one wave (runs at full size: mean 26,
+// longest a few above 96).  3 x 3 measured fastest at full size (3.00 us per
+// step; 4 x 4: 3.14, 2 x 3: 3.08, 3 x 2: 3.24, 2 x 2: 3.21): 16 warps x 3
+// spikes cover a mean step (46 spikes) in one round.
+constexpr int kRunWave = 3;
+constexpr int kBatchSpikes = 3;
 constexpr uint32_t kPopWords = kMaxPop * kWCodes;   // weight-table entries per target population
 
 // ---------------------------------------------------------------------------
@@ -252,6 +257,38 @@ __device__ __forceinline__ void store_runs(const StepParams& sp, int c, const ui
         }
 }
 
+// The run bounds of one partition's first kInline spikes of step tb, looked
+// up from the message head as loaded before A(tb + 1): valid (ok) only if the
+// head and each of those id words already carried the tag tb + 1.
+struct EarlyRuns {
+    bool ok;
+    uint32_t b[kInline], e[kInline];
+};
+
+__device__ __forceinline__ void early_runs(const StepParams& sp, int c, const ulonglong2 (&pre)[4],
+                                           uint32_t tag, EarlyRuns& er) {
+    if (tag_of(pre[0].x) != tag) return;
+    const uint32_t g = min((uint32_t)pre[0].x, (uint32_t)kInline);
+    const unsigned long long w[kInline] = {pre[0].y, pre[1].x, pre[1].y, pre[2].x,
+                                           pre[2].y, pre[3].x, pre[3].y};
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < kInline; ++i)
+        if ((uint32_t)i < g && tag_of(w[i]) != tag) ok = false;
+    if (!ok) return;
+    const size_t stride = (size_t)sp.n_part + 1;
+#pragma unroll
+    for (int i = 0; i < kInline; ++i) {
+        er.b[i] = er.e[i] = 0u;
+        if ((uint32_t)i < g) {
+            const uint32_t* sg = sp.seg + (size_t)(uint32_t)w[i] * stride + c;
+            er.b[i] = __ldg(sg);
+            er.e[i] = __ldg(sg + 1);
+        }
+    }
+    er.ok = true;
+}
+
 // ---------------------------------------------------------------------------
 // delivery of the spikes of step tb (message tag tb+1) into this CTA's ring;
 // returns false if a wait timed out or another CTA aborted
@@ -261,7 +298,8 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
                                              const SmemLayout& L, int c, uint32_t wbase,
                                              int64_t tb, int32_t* ring, int32_t* wrap,
                                              unsigned long long& events,
-                                             const ulonglong2 (&pre)[4]) {
+                                             const ulonglong2 (&pre)[4],
+                                             const EarlyRuns& early) {
     const int tid = threadIdx.x;
     const int P = sp.n_part;
     const int list = (int)(tb & 3);
@@ -331,17 +369,27 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
     if (tid < P && my_cnt > 0u) {
         const uint32_t at = atomicAdd(const_cast<uint32_t*>(&s_misc[3]), my_cnt);
         if (at + my_cnt <= (uint32_t)kChunk) {
-            uint32_t ids[kInline];
+            if (early.ok) {                          // bounds looked up during A(tb + 1)
 #pragma unroll
-            for (int i = 0; i < kInline; ++i) {
-                ids[i] = 0u;                         // in range if a wait gives up
-                if ((uint32_t)i < my_cnt) {
-                    unsigned long long e = s_inl[tid * kInline + i];
-                    if (poll_word(sp, m_mine + 1 + i, tag, e)) ids[i] = (uint32_t)e;
-                    else s_misc[2] = 1u;
+                for (int i = 0; i < kInline; ++i)
+                    if ((uint32_t)i < my_cnt) {
+                        s_rb[at + i] = early.b[i];
+                        s_rl[at + i] = early.e[i] - early.b[i];
+                    }
+            } else {
+                uint32_t ids[kInline];
+#pragma unroll
+                for (int i = 0; i < kInline; ++i) {
+                    ids[i] = 0u;                     // in range if a wait gives up
+                    if ((uint32_t)i < my_cnt) {
+                        unsigned long long e = s_inl[tid * kInline + i];
+                        if (poll_word(sp, m_mine + 1 + i, tag, e)) ids[i] = (uint32_t)e;
+                        else s_misc[2] = 1u;
+                    }
                 }
+                store_runs<kInline>(sp, c, ids, min(my_cnt, (uint32_t)kInline), s_rb + at,
+                                    s_rl + at);
             }
-            store_runs<kInline>(sp, c, ids, min(my_cnt, (uint32_t)kInline), s_rb + at, s_rl + at);
             for (uint32_t i = kInline; i < my_cnt; i += 8) {
                 ulonglong2 v[4];                     // entries 1+i.. are 16-B aligned
 #pragma unroll
@@ -443,6 +491,9 @@ __global__ void __launch_bounds__(kStepThreads, 1)
 k_step(const __grid_constant__ StepParams sp) {
     constexpr bool PACED = (MODE & kModePaced) != 0;
     constexpr bool SAT = (MODE & kModeSat) != 0;
+    // early run lookups keep 2 x kInline more registers live across the
+    // background draw: only in the one-neuron-per-thread variant
+    constexpr bool EARLY = NPT == 1;
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -578,6 +629,16 @@ k_step(const __grid_constant__ StepParams sp) {
                     }
                 }
             }
+        }
+        // the run bounds of the step t-1 spikes whose message words this
+        // header thread already holds (the head loaded before A(t)): looked
+        // up now, so that they return while the background is drawn
+        EarlyRuns early;
+        early.ok = false;
+        if (EARLY && s > 0 && tid < P) early_runs(sp, c, pre, (uint32_t)t, early);
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int li = tid + k * kStepThreads;
             // background count of step t (independent of the network): drawn
             // here, added to the ring input in C(t)
             if (sp.mode == 0 && li < nc) {
@@ -615,7 +676,7 @@ k_step(const __grid_constant__ StepParams sp) {
         ras_base += nsp;
         // ---- D: spikes of step t-1 ----
         if (s > 0) {
-            if (!deliver_list<SAT>(sp, smem, L, c, wt_base, t - 1, ring, wrap, events, pre)) {
+            if (!deliver_list<SAT>(sp, smem, L, c, wt_base, t - 1, ring, wrap, events, pre, early)) {
                 aborted = true;
                 break;
             }
@@ -672,7 +733,9 @@ k_step(const __grid_constant__ StepParams sp) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) pre[q] = __ldcg(reinterpret_cast<const ulonglong2*>(m + 2 * q));
         }
-        deliver_list<SAT>(sp, smem, L, c, wt_base, tl, ring, wrap, events, pre);
+        EarlyRuns none;
+        none.ok = false;
+        deliver_list<SAT>(sp, smem, L, c, wt_base, tl, ring, wrap, events, pre, none);
     }
     __syncthreads();
 #pragma unroll
