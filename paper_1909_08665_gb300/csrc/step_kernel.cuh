@@ -629,16 +629,6 @@ k_step(const __grid_constant__ StepParams sp) {
                     }
                 }
             }
-        }
-        // the run bounds of the step t-1 spikes whose message words this
-        // header thread already holds (the head loaded before A(t)): looked
-        // up now, so that they return while the background is drawn
-        EarlyRuns early;
-        early.ok = false;
-        if (EARLY && s > 0 && tid < P) early_runs(sp, c, pre, (uint32_t)t, early);
-#pragma unroll
-        for (int k = 0; k < NPT; ++k) {
-            const int li = tid + k * kStepThreads;
             // background count of step t (independent of the network): drawn
             // here, added to the ring input in C(t)
             if (sp.mode == 0 && li < nc) {
@@ -658,6 +648,13 @@ k_step(const __grid_constant__ StepParams sp) {
                 pacc[k] = kk * sp.wext_q;
             }
         }
+        // the run bounds of the step t-1 spikes whose message words this
+        // header thread already holds (the head loaded before A(t), arrived
+        // by now): looked up here, so that they return while the CTA meets
+        // at the barrier and the header is published
+        EarlyRuns early;
+        early.ok = false;
+        if (EARLY && s > 0 && tid < P) early_runs(sp, c, pre, (uint32_t)t, early);
         __syncthreads();
         const uint32_t nsp = *my_cnt;
         if (tid == 0) {
