@@ -153,8 +153,8 @@ k_deliver_part(const __grid_constant__ StepParams sp, const uint32_t* __restrict
             s_rl[k] = __ldg(sg + 1) - b;
         }
         __syncthreads();
-        deliver_batches<false>(sp, s_rb, s_rl, s_w, wbase, (uint32_t)m, t, ring, nullptr, events,
-                               nullptr);
+        deliver_batches<false, BatchShape<1>::kSpikes, BatchShape<1>::kWave>(
+            sp, s_rb, s_rl, s_w, wbase, (uint32_t)m, t, ring, nullptr, events, nullptr);
         __syncthreads();
     }
     if (SMEM_RING)

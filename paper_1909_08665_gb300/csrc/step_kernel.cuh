@@ -25,7 +25,7 @@
 //         its own tag, so a matching tag is both the grid-wide barrier and
 //         the data; no fence, no counter), look up each spike's run for this
 //         partition and deliver those spikes into ring slots t-1+d (d >= 1):
-//         per warp, batches of kBatchSpikes spikes whose runs are all loaded
+//         per warp, batches of a few spikes whose runs are all loaded
 //         before the shared-memory atomics.
 //   C(t)  acc = ring[t] (cleared) + background; I_t = P11 I_{t-1} + acc/256.
 // A(t+1) needs only I_t, and the spikes of step t reach no input before
@@ -51,13 +51,18 @@ namespace snn {
 constexpr int kWarps = kStepThreads / 32;
 constexpr uint32_t kStatusRasterOverflow = 2u;
 constexpr int kInline = 7;              // ids read together with a message header (64 B)
-// a warp takes kBatchSpikes spikes at once and loads the first 32 kRunWave
-// entries of each of their runs in one wave (runs at full size: mean 26,
-// longest a few above 96).  3 x 3 measured fastest at full size (3.00 us per
-// step; 4 x 4: 3.14, 2 x 3: 3.08, 3 x 2: 3.24, 2 x 2: 3.21): 16 warps x 3
-// spikes cover a mean step (46 spikes) in one round.
-constexpr int kRunWave = 3;
-constexpr int kBatchSpikes = 3;
+// A warp takes BATCH spikes at once and loads the first 32 WAVE entries of
+// each of their runs in one wave (runs: mean 26 entries at scale 1 and 4,
+// rarely above 96).  Measured at full size (one neuron per thread), 3 x 3 is
+// fastest (3.00 us per step; 4 x 4: 3.14, 2 x 3: 3.08, 3 x 2: 3.24, 2 x 2:
+// 3.21): 16 warps x 3 spikes cover a mean step (46 spikes) in one round.  At
+// 4x (4 neurons per thread, 177 spikes per step) 8 x 3 is (14.3 us; 4 x 4:
+// 14.5, 3 x 3: 15.9, 6 x 4: 16.0, 8 x 4: 16.4).
+template <int NPT>
+struct BatchShape {
+    static constexpr int kSpikes = NPT == 1 ? 3 : 8;
+    static constexpr int kWave = 3;
+};
 constexpr uint32_t kPopWords = kMaxPop * kWCodes;   // weight-table entries per target population
 
 // ---------------------------------------------------------------------------
@@ -153,7 +158,7 @@ __device__ inline bool poll_word(const StepParams& sp, const unsigned long long*
 
 // ---------------------------------------------------------------------------
 // the runs s_rb/s_rl[0, m) of the spikes of step tb into this CTA's ring:
-// batches of kBatchSpikes spikes per warp.  Entry x of a run (a pre-decoded synapse) is
+// batches of kBatchSpikes spikes per warp (BatchShape).  Entry x of a run (a pre-decoded synapse) is
 // the weight-table index x >> kPreOffBits and the ring offset
 // x & kPreOffMask = delay * ncmax + local target; its weight, looked up in
 // s_w (table rows from population p_lo on, wbase = p_lo * kPopWords), is
@@ -184,7 +189,7 @@ __device__ __forceinline__ void add_entry(uint32_t x, const int32_t* s_w, uint32
 
 // s_cnt (non-null while per-step counts are recorded): the list's synaptic
 // events and its non-empty runs are added into s_cnt[0], s_cnt[1]
-template <bool SAT>
+template <bool SAT, int kBatchSpikes, int kRunWave>
 __device__ __forceinline__ void deliver_batches(const StepParams& sp, const uint32_t* s_rb,
                                                 const uint32_t* s_rl, const int32_t* s_w,
                                                 uint32_t wbase, uint32_t m, int64_t tb,
@@ -293,7 +298,7 @@ __device__ __forceinline__ void early_runs(const StepParams& sp, int c, const ul
 // delivery of the spikes of step tb (message tag tb+1) into this CTA's ring;
 // returns false if a wait timed out or another CTA aborted
 // ---------------------------------------------------------------------------
-template <bool SAT>
+template <bool SAT, int BATCH, int WAVE>
 __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char* smem,
                                              const SmemLayout& L, int c, uint32_t wbase,
                                              int64_t tb, int32_t* ring, int32_t* wrap,
@@ -416,7 +421,8 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
     const uint32_t S_fast = s_misc[3];
     if (s_misc[2]) return false;
     if (S_fast <= (uint32_t)kChunk) {
-        deliver_batches<SAT>(sp, s_rb, s_rl, s_w, wbase, S_fast, tb, ring, wrap, events, s_cnt);
+        deliver_batches<SAT, BATCH, WAVE>(sp, s_rb, s_rl, s_w, wbase, S_fast, tb, ring, wrap, events,
+                                          s_cnt);
         __syncthreads();
         if (tid == 0) s_misc[3] = 0u;
         flush_counts(S_fast);
@@ -453,7 +459,8 @@ __device__ __forceinline__ bool deliver_list(const StepParams& sp, unsigned char
             }
         }
         __syncthreads();
-        deliver_batches<SAT>(sp, s_rb, s_rl, s_w, wbase, m, tb, ring, wrap, events, s_cnt);
+        deliver_batches<SAT, BATCH, WAVE>(sp, s_rb, s_rl, s_w, wbase, m, tb, ring, wrap, events,
+                                          s_cnt);
         __syncthreads();
     }
     flush_counts(S);
@@ -673,7 +680,8 @@ k_step(const __grid_constant__ StepParams sp) {
         ras_base += nsp;
         // ---- D: spikes of step t-1 ----
         if (s > 0) {
-            if (!deliver_list<SAT>(sp, smem, L, c, wt_base, t - 1, ring, wrap, events, pre, early)) {
+            if (!deliver_list<SAT, BatchShape<NPT>::kSpikes, BatchShape<NPT>::kWave>(
+                    sp, smem, L, c, wt_base, t - 1, ring, wrap, events, pre, early)) {
                 aborted = true;
                 break;
             }
@@ -732,7 +740,8 @@ k_step(const __grid_constant__ StepParams sp) {
         }
         EarlyRuns none;
         none.ok = false;
-        deliver_list<SAT>(sp, smem, L, c, wt_base, tl, ring, wrap, events, pre, none);
+        deliver_list<SAT, BatchShape<NPT>::kSpikes, BatchShape<NPT>::kWave>(
+            sp, smem, L, c, wt_base, tl, ring, wrap, events, pre, none);
     }
     __syncthreads();
 #pragma unroll
