@@ -58,6 +58,7 @@ METRIC = "real-time factor and synaptic events/s (full microcircuit, 1 GB300); %
 UNIT = "synaptic events/s"
 STEPS_PER_BENCH_STEP = 10000          # 1 s of biological time at dt = 0.1 ms
 BYTES_PER_EVENT = 4                   # one packed synaptic word read per event
+TILING_NAMES = ["warp", "block", "partition", "words", "cluster", "stream"]   # snn_deliver tilings
 # DRAM bytes (read + write) per synaptic event of k_step, from one ncu capture
 # of the current kernel on the small case (scale 0.4: dram__bytes_read.sum +
 # dram__bytes_write.sum of one 2000-step launch that delivered 19,040.77
@@ -694,7 +695,7 @@ def run_deliver(args):
                     if err.code != pkg.SNN_ERR_UNSUPPORTED:
                         raise
                     rows.append({"scale": scale, "spikes": m,
-                                 "tiling": ["warp", "block", "partition", "words", "cluster"][tiling],
+                                 "tiling": TILING_NAMES[tiling],
                                  "unsupported": str(err)})
                     continue
                 torch.cuda.synchronize()
@@ -710,7 +711,7 @@ def run_deliver(args):
                 ev = float(np.mean(events[:reps]))
                 gbs = 4.0 * ev / (ms * 1e-3) / 1e9
                 rows.append({"scale": scale, "spikes": m,
-                             "tiling": ["warp", "block", "partition", "words", "cluster"][tiling],
+                             "tiling": TILING_NAMES[tiling],
                              "us": ms * 1e3, "events": ev, "achieved_gbs": gbs,
                              "frac": gbs / hbm_peak})
         net.close()

@@ -275,7 +275,12 @@ int snn_export_network(snn_net* net, uint64_t* row_ptr_host, uint32_t* words_hos
  * 4: clusters of 8 CTAs,
  * one partition's ring slice in each CTA's shared memory, every row read once
  * per cluster and added through distributed shared memory
- * (SNN_ERR_UNSUPPORTED when a ring slice and the weight table do not fit).
+ * (SNN_ERR_UNSUPPORTED when a ring slice and the weight table do not fit);
+ * 5: one CTA per partition reading the same runs as tiling 3, streamed into
+ * shared memory by bulk copies (one producer warp, mbarrier-completed stages)
+ * and added by the other warps (SNN_ERR_UNSUPPORTED when the ring slice and
+ * the stages do not fit in shared memory).  A wait of tiling 5 that runs out
+ * makes snn_sync report SNN_ERR_TIMEOUT.  Spike ids must be below n_neurons.
  * Asynchronous on the network's stream; adds to the existing ring content.
  */
 int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int64_t t,

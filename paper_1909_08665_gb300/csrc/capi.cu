@@ -911,7 +911,7 @@ int snn_export_network(snn_net* net, uint64_t* row_ptr_host, uint32_t* words_hos
 
 int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int64_t t,
                 int32_t tiling) {
-    if (!net || n_spikes < 0 || (n_spikes > 0 && !spikes_dev) || tiling < 0 || tiling > 4)
+    if (!net || n_spikes < 0 || (n_spikes > 0 && !spikes_dev) || tiling < 0 || tiling > 5)
         return fail(SNN_ERR_INVALID, "bad arguments");
     if (tiling == 2) {
         StepParams sp;
@@ -935,7 +935,16 @@ int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int6
     dp.wtab = net->d_wtab;
     dp.ring = net->d_ring;
     dp.counters = net->d_counters;
-    if (tiling == 4) {
+    dp.status = net->d_sync + 4;
+    dp.pre = net->d_pre;
+    if (tiling == 5) {
+        int dev = 0, optin = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (deliver_stream_smem(net->ncmax, net->w_span) > (size_t)optin)
+            return fail(SNN_ERR_UNSUPPORTED, "ring slices too large for the streamed delivery");
+        CK(launch_deliver_stream(dp, net->w_span, net->stream));
+    } else if (tiling == 4) {
         int active = 0;
         if (deliver_cluster_check(net->ncmax, net->P, &active) != cudaSuccess || active < 1) {
             cudaGetLastError();
@@ -943,7 +952,6 @@ int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int6
         }
         CK(launch_deliver_cluster(dp, net->stream));
     } else if (tiling == 3) {
-        dp.pre = net->d_pre;
         CK(launch_deliver_words(dp, net->stream));
     } else {
         CK(launch_deliver(dp, tiling, net->stream));

@@ -221,6 +221,7 @@ struct DeliverParams {
     const int32_t* wtab;
     int32_t* ring;
     unsigned long long* counters;
+    uint32_t* status;             // ORed with the timeout bit if a bounded wait gives up
 };
 
 __device__ __forceinline__ int pop_index(const int32_t* pop_start, int n_pop, int32_t i) {
@@ -278,6 +279,10 @@ constexpr uint32_t kPreOffBits = 19;
 constexpr uint32_t kPreOffMask = (1u << kPreOffBits) - 1u;
 cudaError_t launch_predecode(const DeliverParams& dp, const unsigned long long* row_start,
                              uint32_t* pre, cudaStream_t s);
+// stand-alone delivery of the exact runs streamed into shared memory by bulk
+// copies (one producer warp, consumer warps; ring slice in shared memory)
+size_t deliver_stream_smem(int ncmax, int w_span);
+cudaError_t launch_deliver_stream(const DeliverParams& dp, int w_span, cudaStream_t s);
 // stand-alone delivery through clusters of 8 CTAs (rings in distributed
 // shared memory); needs the ring slice and the weight table in shared memory
 cudaError_t launch_deliver_cluster(const DeliverParams& dp, cudaStream_t s);

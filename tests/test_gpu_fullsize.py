@@ -75,7 +75,7 @@ def test_full_size_delivery_every_tiling(full, n_spikes):
     onet = oracle.Network(cfg, n_threads=os.cpu_count())
     first = workload.random_spike_list(net.n, 500, seed=5).astype(np.int32)
     d_first = torch.from_numpy(first).cuda()
-    for tiling in (0, 1, 2, 3, 4):
+    for tiling in (0, 1, 2, 3, 4, 5):
         fresh = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
         spikes = workload.random_spike_list(fresh.n, n_spikes, seed=11 + tiling).astype(np.int32)
         d = torch.from_numpy(spikes).cuda()
@@ -169,6 +169,11 @@ def test_scale4_short_run_bit_exact():
             np.testing.assert_array_equal(fresh.ring(), ref)
             fresh.close()
         del ref
+    fresh = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
+    with pytest.raises(pkg.SnnError) as e:          # ring slices too large for the stages
+        fresh.deliver(d.data_ptr(), spikes.size, 4321, 5)
+    assert e.value.code == pkg.SNN_ERR_UNSUPPORTED
+    fresh.close()
 
 
 def test_full_scale_statistics_agree_with_oracle_seeds():

@@ -199,7 +199,7 @@ def test_empty_network_and_zero_steps():
 # standalone delivery: every tiling against the oracle
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("n_spikes", [1, 25, 93, 4000])
-@pytest.mark.parametrize("tiling", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("tiling", [0, 1, 2, 3, 4, 5])
 def test_deliver_matches_oracle(cfg01, onet01, n_spikes, tiling):
     net = gpu_net(cfg01)
     spikes = workload.random_spike_list(net.n, n_spikes, seed=n_spikes)
@@ -226,9 +226,10 @@ def test_deliver_partition_tilings_with_global_ring(cfg01, onet01):
         np.testing.assert_array_equal(net.ring(), ref)
         net.close()
     net = gpu_net(cfg01, n_part=2)               # ring slices too large for clusters
-    with pytest.raises(pkg.SnnError) as e:
-        net.deliver(d.data_ptr(), spikes.size, 77, 4)
-    assert e.value.code == pkg.SNN_ERR_UNSUPPORTED
+    for tiling in (4, 5):                        # and for the streamed stages
+        with pytest.raises(pkg.SnnError) as e:
+            net.deliver(d.data_ptr(), spikes.size, 77, tiling)
+        assert e.value.code == pkg.SNN_ERR_UNSUPPORTED
 
 
 def test_realtime_pacing_keeps_the_wall_clock_and_the_results(cfg01):
