@@ -7,8 +7,10 @@
 // range [goff_k, goff_k + n_k).  CTA b owns the contiguous range
 // [b * chunk, (b + 1) * chunk), chunk = ceil(total / CTAs) <= 512 NPT, and keeps u, I and the refractory
 // counter of its neurons in registers; the four cached background draws of
-// each neuron sit in shared memory.  The 64-slot ring buffers of all neurons
-// are one global array [slot][global neuron].
+// each neuron sit in shared memory.  The ring buffers of all neurons are one
+// global array [slot][global neuron] of R slots, R = the longest delay of any
+// instance + 1 (38 for the benchmark's delays: the 64-instance ring, 111 MB,
+// fits in L2 where 64 slots would not); step t owns slot t mod R.
 //
 // Per step t the work is A(t) (membrane update u_t with I_{t-1}, threshold,
 // reset, refractory; spikes appended to the list of step t), D(t) (delivery
@@ -17,7 +19,7 @@
 // I_t, and C(t) needs the deliveries of step t - 1, so one grid barrier per
 // step suffices:
 //     A(t0);  for t: { barrier; D(t); C(t); A(t + 1) }
-// D(t) writes slots t + 1 .. t + 63 while C(t) reads slot t; the lists and
+// D(t) writes slots t + 1 .. t + R - 1 (mod R) while C(t) reads slot t; the lists and
 // their counters rotate over 2 and 4 step parities, so each buffer is reset
 // or rewritten only after the barrier that ends its last reader's phase.
 // Every result equals the single-network path bit for bit (same fp32
@@ -78,6 +80,7 @@ struct InstCold {
 
 struct BatchParams {
     int32_t n_inst, ntot, n_steps;
+    int32_t ring_depth;                 // D: slots of the ring, the longest delay + 1
     int32_t chunk;                      // neurons per CTA (<= NPT * kBThreads)
     int32_t inject_fault;               // 1: CTA 0 never arrives at a barrier
     uint64_t timeout_ns;
@@ -91,7 +94,7 @@ struct BatchParams {
     float* u;
     float* i_syn;
     int32_t* refr;
-    int32_t* ring;                      // [64][ntot]
+    int32_t* ring;                      // [D][ntot]
     uint32_t* list;                     // [2 parity][3 tiling][ntot] global ids
     uint32_t* cnt;                      // [4 parity][3 tiling]
     uint32_t* ras_step;
@@ -123,9 +126,15 @@ __device__ __forceinline__ bool grid_sync(const BatchParams& p, uint32_t& gen,
 
 // Row of global neuron gi, emitted at step t, added into ring slots t + d by
 // `lanes` cooperating threads (rank r among them), U words in flight each.
+// tD = t mod D; a synapse of delay d (1 <= d < D) adds into slot (tD + d) mod D
+__device__ __forceinline__ uint32_t ring_slot(uint32_t tD, uint32_t d, uint32_t D) {
+    const uint32_t sl = tD + d;
+    return sl >= D ? sl - D : sl;
+}
+
 template <int U>
 __device__ __forceinline__ void deliver_row(const BatchParams& p, const int32_t* s_goff, int32_t gi,
-                                            long long t, int r, int lanes, bool count) {
+                                            uint32_t tD, int r, int lanes, bool count) {
     const int ki = inst_of(s_goff, p.n_inst, gi);
     const InstCold& I = p.cold[ki];
     const int32_t j = gi - I.goff;
@@ -156,7 +165,7 @@ __device__ __forceinline__ void deliver_row(const BatchParams& p, const int32_t*
 #pragma unroll
                 for (int k = 1; k < kMaxPop; ++k) pp += tgt >= ps[k] ? 1 : 0;
                 const int32_t wt = __ldg(&wq[pp * (kMaxPop * kWCodes) + (int)(w[u] >> 25)]);
-                const uint32_t slot = (uint32_t)(t + ((w[u] >> kTgtBits) & 63u)) & (kRing - 1);
+                const uint32_t slot = ring_slot(tD, (w[u] >> kTgtBits) & 63u, (uint32_t)p.ring_depth);
                 atomicAdd(&rbase[(size_t)slot * ntot + tgt], wt);
             }
         }
@@ -195,7 +204,7 @@ __device__ inline void flat_load_ps(const BatchParams& p, const FlatSmem& F) {
 // Flat tiling: the rows of the nf spikes in `list`, spread over every warp of
 // the grid.  Every CTA stages the same rows; CTA 0 alone counts the events.
 __device__ void deliver_flat(const BatchParams& p, const int32_t* s_goff, const FlatSmem& F,
-                             const uint32_t* list, uint32_t nf, long long t, bool count) {
+                             const uint32_t* list, uint32_t nf, uint32_t tD, bool count) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t ntot = (size_t)p.ntot;
     for (uint32_t f0 = 0; f0 < nf; f0 += kFlatChunk) {
@@ -278,7 +287,7 @@ __device__ void deliver_flat(const BatchParams& p, const int32_t* s_goff, const 
                     for (int m = 1; m < kMaxPop; ++m) pp += tgt >= F.ps[ki * 8 + m] ? 1 : 0;
                     const int32_t wt = __ldg(&p.wtab_all[(((size_t)ki * kMaxPop + pp) * kMaxPop + q) *
                                                          kWCodes + (word[u] >> 25)]);
-                    const uint32_t slot = (uint32_t)(t + ((word[u] >> kTgtBits) & 63u)) & (kRing - 1);
+                    const uint32_t slot = ring_slot(tD, (word[u] >> kTgtBits) & 63u, (uint32_t)p.ring_depth);
                     atomicAdd(&p.ring[(size_t)slot * ntot + s_goff[ki] + tgt], wt);
                 }
             }
@@ -398,6 +407,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ 
     uint32_t gen = 0;
     for (int s = 0; s < n; ++s) {
         const long long t = t0 + s;
+        const uint32_t tD = (uint32_t)(t % p.ring_depth);
         if (!grid_sync(p, gen, &s_abort)) break;
         // counters of step t + 2: last read in D(t - 2), next written in A(t + 2)
         if (blockIdx.x == 0 && tid < kTilings) p.cnt[(uint32_t)((t + 2) & 3) * kTilings + tid] = 0u;
@@ -411,20 +421,19 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ 
             const uint32_t* lw = p.list + ((size_t)par2 * kTilings + 0) * ntot;
             const uint32_t* lb = p.list + ((size_t)par2 * kTilings + 1) * ntot;
             const uint32_t* lf = p.list + ((size_t)par2 * kTilings + 2) * ntot;
-            if (nf) deliver_flat(p, s_goff, F, lf, nf, t, true);
+            if (nf) deliver_flat(p, s_goff, F, lf, nf, tD, true);
             // warp w of CTA b takes spikes w * grid + b, spreading them over SMs
             for (uint32_t k = (uint32_t)(tid >> 5) * gridDim.x + blockIdx.x; k < nw;
                  k += (uint32_t)kBWarps * gridDim.x)
-                deliver_row<kWarpUnroll>(p, s_goff, (int32_t)__ldcg(&lw[k]), t, lane, 32, true);
+                deliver_row<kWarpUnroll>(p, s_goff, (int32_t)__ldcg(&lw[k]), tD, lane, 32, true);
             // CTA rows start from the last CTA, away from the first warp rows
             for (uint32_t k = gridDim.x - 1u - blockIdx.x; k < nb; k += gridDim.x)
-                deliver_row<kBlockUnroll>(p, s_goff, (int32_t)__ldcg(&lb[k]), t, tid, kBThreads, true);
+                deliver_row<kBlockUnroll>(p, s_goff, (int32_t)__ldcg(&lb[k]), tD, tid, kBThreads, true);
         }
 
         // ---- C(t): ring slot t, background, synaptic current ----
         {
-            const uint32_t slot = (uint32_t)t & (kRing - 1);
-            int32_t* rs = p.ring + (size_t)slot * ntot;
+            int32_t* rs = p.ring + (size_t)tD * ntot;
             int32_t acc[NPT];
 #pragma unroll
             for (int k = 0; k < NPT; ++k)
@@ -536,6 +545,7 @@ struct snn_batch {
     int ntot = 0;
     int npt = 0;
     int blocks = 0;
+    int ring_depth = 2;                  // ring slots: the longest delay of any instance + 1
     size_t smem = 0;
     cudaStream_t stream = nullptr;
     std::vector<int32_t> goff;
@@ -682,7 +692,7 @@ int autotune(snn_batch* b) {
     cudaFree(d_spk);
     if (e != cudaSuccess) return set_cuda_error(e, "autotune");
     // the probes added into the ring: clear it again
-    BCK(cudaMemsetAsync(b->d_ring, 0, sizeof(int32_t) * (size_t)kRing * b->ntot, s));
+    BCK(cudaMemsetAsync(b->d_ring, 0, sizeof(int32_t) * (size_t)b->ring_depth * b->ntot, s));
     BCK(cudaMemcpyAsync(b->d_hot, b->hot_h.data(), sizeof(InstHot) * b->n_inst,
                         cudaMemcpyHostToDevice, s));
     BCK(cudaStreamSynchronize(s));
@@ -695,7 +705,7 @@ cudaError_t reset_state(snn_batch* b) {
     const size_t ntot = (size_t)b->ntot;
     cudaError_t e = cudaMemsetAsync(b->d_i, 0, sizeof(float) * ntot, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_r, 0, sizeof(int32_t) * ntot, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ring, 0, sizeof(int32_t) * (size_t)kRing * ntot, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ring, 0, sizeof(int32_t) * (size_t)b->ring_depth * ntot, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cnt, 0, sizeof(uint32_t) * 4 * kTilings, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ras_n, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ic, 0, sizeof(unsigned long long) * 2 * b->n_inst, s);
@@ -840,6 +850,7 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
         HostTables ht;
         rc = host_tables(&cfgs[k], &ht);
         if (rc != SNN_OK) break;
+        b->ring_depth = std::max(b->ring_depth, (int)ht.max_delay + 1);
         InstHot& H = b->hot_h[k];
         InstCold& C = b->cold_h[k];
         std::memset(&H, 0, sizeof(H));
@@ -950,7 +961,7 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
     if (rc == SNN_OK) rc = balloc(&b->d_u, ntot, "batch u");
     if (rc == SNN_OK) rc = balloc(&b->d_i, ntot, "batch I");
     if (rc == SNN_OK) rc = balloc(&b->d_r, ntot, "batch refractory counters");
-    if (rc == SNN_OK) rc = balloc(&b->d_ring, (size_t)kRing * ntot, "batch ring buffers");
+    if (rc == SNN_OK) rc = balloc(&b->d_ring, (size_t)b->ring_depth * ntot, "batch ring buffers");
     if (rc == SNN_OK) rc = balloc(&b->d_list, (size_t)2 * kTilings * ntot, "batch spike lists");
     if (rc == SNN_OK) rc = balloc(&b->d_cnt, 4 * kTilings, "batch list counters");
     if (rc == SNN_OK) rc = balloc(&b->d_ras_step, b->ras_cap, "batch raster");
@@ -975,7 +986,7 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
         e = cudaMemcpyAsync(b->d_cdc, cdc.data(), sizeof(float) * cdc.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_i, 0, sizeof(float) * ntot, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_r, 0, sizeof(int32_t) * ntot, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ring, 0, sizeof(int32_t) * (size_t)kRing * ntot, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ring, 0, sizeof(int32_t) * (size_t)b->ring_depth * ntot, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cnt, 0, sizeof(uint32_t) * 4 * kTilings, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ras_n, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ic, 0, sizeof(unsigned long long) * 2 * n_inst, s);
@@ -995,6 +1006,7 @@ int snn_batch_create(const snn_config* cfgs, const uint64_t* seeds, int32_t n_in
     std::memset(&p, 0, sizeof(p));
     p.n_inst = n_inst;
     p.ntot = b->ntot;
+    p.ring_depth = b->ring_depth;
     p.chunk = (int32_t)(((long long)b->ntot + b->blocks - 1) / b->blocks);
     p.timeout_ns = (uint64_t)(((opt && opt->timeout_s > 0) ? opt->timeout_s : 2.0) * 1e9);
     p.inject_fault = opt ? opt->inject_fault : 0;

@@ -496,6 +496,9 @@ int host_tables(const snn_config* cfg, HostTables* out) {
     out->wext_q = tmp.wext_q;
     out->n_ref = tmp.n_ref;
     out->mode = cfg->input_mode;
+    out->max_delay = 1;
+    for (int q = 0; q < cfg->n_pop; ++q)
+        for (int k = 0; k < kDCodes; ++k) out->max_delay = std::max(out->max_delay, (int32_t)tmp.dtab[q * kDCodes + k]);
     return SNN_OK;
 }
 

@@ -141,6 +141,7 @@ struct HostTables {
     float cdc[kMaxPop];
     float theta;
     int32_t wext_q, n_ref, mode;
+    int32_t max_delay;                  // longest delay (steps) of any synapse
 };
 
 struct StepParams {

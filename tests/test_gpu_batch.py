@@ -133,6 +133,32 @@ def test_batch_of_64_uneven_instances():
     b.close()
 
 
+def _with_delays(cfg, d_mean, d_sd):
+    c = dict(cfg)
+    c["d_mean"] = [d_mean] * 8
+    c["d_sd"] = [d_sd] * 8
+    return c
+
+
+@pytest.mark.parametrize("long_delays", [False, True])
+def test_batch_ring_depth_follows_longest_delay(long_delays):
+    """The batch ring has one slot more than the longest delay of any
+    instance: with delays of 1..3 steps it wraps every few steps; with one
+    instance whose delays reach the 63-step cap beside them, all 64 slots are
+    in use.  Every instance bit for bit against the oracle."""
+    cfgs = [_with_delays(workload.microcircuit(0.03, seed=61), 0.2, 0.05),
+            _with_delays(workload.microcircuit(0.02, seed=62), 0.15, 0.05)]
+    if long_delays:
+        cfgs.append(_with_delays(workload.microcircuit(0.025, seed=63), 3.0, 1.5))
+    steps = 300
+    b = pkg.MicrocircuitBatch(cfgs, stream=torch.cuda.current_stream())
+    b.step(steps)
+    b.sync()
+    for k, cfg in enumerate(cfgs):
+        _assert_instance_equal(b, k, _oracle_run(cfg, steps))
+    b.close()
+
+
 def test_batch_barrier_timeout_is_reported():
     cfgs = _mixed_instances()[:2]
     b = pkg.MicrocircuitBatch(cfgs, stream=torch.cuda.current_stream(), timeout_s=0.05,
