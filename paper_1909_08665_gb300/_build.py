@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsnn_gb300.so")
 SOURCES = ["capi.cu", "build_net.cu", "step.cu", "step_mode_plain.cu", "step_mode_paced.cu",
            "step_mode_sat.cu", "step_mode_sat_paced.cu", "noalloc.cu", "batch.cu", "grad.cu",
-           "deliver_cluster.cu", "deliver_words.cu", "deliver_stream.cu"]
+           "adjoint_part.cu", "deliver_cluster.cu", "deliver_words.cu", "deliver_stream.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-O2"]

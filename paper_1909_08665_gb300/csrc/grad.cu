@@ -68,6 +68,10 @@ struct snn_grad {
     int32_t* order = nullptr;       // [n] each CTA's rows, longest first
     int32_t grid = 0, chunk = 0;    // CTAs of the adjoint, most rows of one CTA
     uint32_t* pre = nullptr;        // pre-decoded rows of the adjoint gather (small networks)
+    bool part_planned = false;      // the partition-local adjoint was considered
+    snn::AdjPartPlan* part = nullptr;   // its plan, when the network fits
+    float* pds = nullptr;           // [2][P][n] its partial spike adjoints
+    double* gAc = nullptr;          // [P][n][8] its partial weight gradients
 };
 
 namespace snn {
@@ -79,6 +83,12 @@ void free_grad(snn_grad* g) {
                     g->pop_start, g->blk, g->order, g->pre};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (g->part) {
+        adjoint_part_free(g->part);
+        delete g->part;
+    }
+    if (g->pds) cudaFree(g->pds);
+    if (g->gAc) cudaFree(g->gAc);
     delete g;
 }
 
@@ -548,6 +558,21 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
         GCK(cudaGetLastError());
     }
 
+    if (!g->part_planned) {
+        // the partition-local gather when every CTA's share of the rows fits
+        // in shared memory
+        AdjPartPlan plan;
+        const int rc = adjoint_part_plan(n, net->n_pop, net->pop_start, P, net->part_lo.data(), net->ncmax,
+                                         net->nnz, net->d_row_start, net->d_pre, net->d_seg, &plan);
+        if (rc < 0) return set_error(SNN_ERR_CUDA, "partition-local adjoint plan");
+        if (rc == 0) {
+            g->part = new AdjPartPlan(plan);
+            GCALL(galloc(&g->pds, (size_t)2 * P * n, "adjoint partials"));
+            GCALL(galloc(&g->gAc, (size_t)P * n * kMaxPop, "gradient partials"));
+        }
+        g->part_planned = true;
+    }
+    if (g->part) GCK(cudaMemsetAsync(g->gAc, 0, sizeof(double) * (size_t)P * n * kMaxPop, s));
     if (!g->blk) {
         // CTA row ranges with equal total row length, rows longest first
         int dev = 0, sms = 0;
@@ -631,9 +656,43 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
         sp.tr_t0 = t0;
         sp.tr_len = len;
         GCK(net_launch(net, sp, t0, len));
+        GCK(cudaMemsetAsync(g->sync, 0, sizeof(uint32_t), s));
+        if (g->part) {
+            AdjPartParams pp;
+            std::memset(&pp, 0, sizeof(pp));
+            pp.n = n;
+            pp.n_pop = net->n_pop;
+            pp.n_part = P;
+            pp.ncmax = net->ncmax;
+            pp.len = len;
+            pp.t_first = t0;
+            pp.P22 = ap.P22;
+            pp.P21 = ap.P21;
+            pp.P11 = ap.P11;
+            pp.theta = ap.theta;
+            for (int k = 0; k < kMaxPop; ++k) pp.gs[k] = ap.gs[k];
+            for (int k = 0; k <= kMaxPop; ++k) pp.pop_start[k] = net->pop_start[k];
+            pp.timeout_ns = ap.timeout_ns;
+            pp.part_lo = net->d_part_lo;
+            pp.wtab = net->d_wtab;
+            pp.wbase = g->wbase;
+            pp.tr_u = g->tr_u;
+            pp.tr_f = g->tr_f;
+            pp.lu = g->lu;
+            pp.lI = g->lI;
+            pp.lring = g->lring;
+            pp.mnext = g->mnext;
+            pp.pds = g->pds;
+            pp.gAc = g->gAc;
+            pp.gN = g->gN;
+            pp.barrier = g->sync;
+            pp.status = g->sync + 1;
+            pp.abort_flag = g->sync + 2;
+            GCK(launch_adjoint_part(*g->part, pp, s));
+            continue;
+        }
         ap.t_first = t0;
         ap.len = len;
-        GCK(cudaMemsetAsync(g->sync, 0, sizeof(uint32_t), s));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(kAdjThreads);
@@ -647,6 +706,8 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
         void* args[] = {&ap};
         GCK(cudaLaunchKernelExC(&cfg, adj_fn, args));
     }
+    if (g->part)
+        GCK(launch_adjoint_part_fold(n, P, net->n_pop, net->d_part_lo, g->pop_start, g->gAc, g->gA, s));
     k_grad_reduce<<<1, 512, 0, s>>>(n, net->n_pop, g->pop_start, g->gA, g->gN, g->out + kMaxPop * kMaxPop + 1,
                                      g->out);
     GCK(cudaGetLastError());

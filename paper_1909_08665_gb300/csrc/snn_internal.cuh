@@ -88,14 +88,17 @@ __device__ __forceinline__ void wait_until_ns(uint64_t target) {
 // another CTA raised the abort flag, or after timeout_ns, when it sets the
 // timeout status bit and the abort flag itself.  skip_arrive withholds this
 // CTA's arrival (tests of the bounded wait).  Returns false once aborted.
+// The arrival is a release reduction by thread 0 after the CTA barrier (it
+// publishes the writes the CTA made before it, and nothing waits for a
+// returned value); the polls are acquire loads, so the CTA sees every write
+// made before the other CTAs' arrivals.
 __device__ __forceinline__ bool grid_barrier(uint32_t* counter, uint32_t* abort_flag,
                                              uint32_t* status, uint64_t timeout_ns,
                                              uint32_t& gen, volatile uint32_t* s_abort,
                                              bool skip_arrive) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        if (!skip_arrive) atomicAdd(counter, 1u);
+        if (!skip_arrive) red_release_gpu_add(counter, 1u);
         const uint32_t target = (gen + 1u) * gridDim.x;
         const uint64_t t_start = globaltimer_ns();
         uint32_t iter = 0;
@@ -110,7 +113,6 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* counter, uint32_t* abort_
                 }
             }
         }
-        __threadfence();
     }
     __syncthreads();
     ++gen;
@@ -288,6 +290,52 @@ cudaError_t launch_deliver_stream(const DeliverParams& dp, int w_span, cudaStrea
 // shared memory); needs the ring slice and the weight table in shared memory
 cudaError_t launch_deliver_cluster(const DeliverParams& dp, cudaStream_t s);
 cudaError_t deliver_cluster_check(int ncmax, int n_part, int* max_active_clusters);
+// The surrogate-gradient adjoint with its row gather done partition by
+// partition in shared memory (adjoint_part.cu): the plan holds, per CTA
+// (partition c, source group g), the runs of its sources into c re-packed for
+// the gather.
+struct AdjPartParams {
+    int32_t n, n_pop, n_part, ncmax, len;
+    int32_t groups, ring_r, span_max, img_max;   // set by launch_adjoint_part
+    int64_t t_first;                 // global step of trace row 0
+    float P22, P21, P11, theta;
+    float gs[kMaxPop];               // dL/ds per spike of each population
+    int32_t pop_start[kMaxPop + 1];
+    uint64_t timeout_ns;
+    const int32_t* part_lo;
+    const uint32_t* img;             // the CTAs' images (set by launch_adjoint_part)
+    const uint32_t* img_off;
+    const int32_t* wtab;             // rounded weights of the forward, 1/256 pA
+    const float* wbase;              // base weights, pA
+    const float* tr_u;
+    const uint8_t* tr_f;
+    float* lu;
+    float* lI;
+    float* lring;                    // [64][n] lI of the last 64 steps
+    uint8_t* mnext;
+    float* pds;                      // [2][n_part][n] partial spike adjoints
+    double* gAc;                     // [n_part][n][8] partial weight gradients
+    double* gN;
+    uint32_t* barrier;
+    uint32_t* status;
+    uint32_t* abort_flag;
+};
+struct AdjPartPlan {
+    int grid = 0, groups = 0, ring_r = 0, span_max = 0;
+    int32_t img_max = 0;             // words of the largest CTA image
+    size_t smem = 0;
+    uint32_t* d_img = nullptr;
+    uint32_t* d_img_off = nullptr;   // [grid + 1]
+};
+// 0: planned; 1: the network does not fit (use the global gather); < 0: error
+int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, const int32_t* part_lo,
+                      int ncmax, uint64_t nnz, const unsigned long long* d_row_start,
+                      const uint32_t* d_pre, const uint32_t* d_seg, AdjPartPlan* plan);
+void adjoint_part_free(AdjPartPlan* plan);
+cudaError_t launch_adjoint_part(const AdjPartPlan& plan, AdjPartParams& ap, cudaStream_t s);
+cudaError_t launch_adjoint_part_fold(int n, int n_part, int n_pop, const int32_t* part_lo,
+                                     const int32_t* pop_start, const double* gAc, double* gA,
+                                     cudaStream_t s);
 // stand-alone delivery through the step kernel's runs (one CTA per partition)
 cudaError_t launch_deliver_part(const StepParams& sp, const uint32_t* spikes, int n, int64_t t,
                                 bool smem_ring, cudaStream_t s);

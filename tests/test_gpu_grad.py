@@ -184,17 +184,21 @@ def assert_gradient_close(ga, gn, ref, rel=1e-3, floor=1e-6):
     assert abs(gn - ref["g_nu"]) <= 1e-4 * abs(ref["g_nu"]), (gn, ref["g_nu"])
 
 
-@pytest.mark.parametrize("t_ref,steps", [(2.0, 100), (0.0, 60)], ids=["t_ref2ms", "t_ref0"])
-def test_surrogate_gradient_short_horizon(t_ref, steps):
+@pytest.mark.parametrize("t_ref,steps,n_part", [(2.0, 100, 0), (0.0, 60, 0), (2.0, 100, 1)],
+                         ids=["t_ref2ms", "t_ref0", "t_ref2ms_one_partition"])
+def test_surrogate_gradient_short_horizon(t_ref, steps, n_part):
     """The cases whose oracle gradient is pinned by central differences of the
     smooth deviation model (2 % network, seed 5): the GPU gradient must match
-    it element by element."""
+    it element by element.  With the default partitions the adjoint gathers
+    partition by partition in shared memory; with one partition spanning all
+    eight populations it takes the global-ring gather."""
     cfg = workload.microcircuit(0.02, seed=5)
     cfg["t_ref"] = t_ref
     targets = workload.target_rates()
     alpha0, nu0 = np.ones((8, 8)), float(cfg["nu_bg"])
     ref = oracle.hard_gradient(cfg, alpha0, nu0, steps, targets, seed=5)
-    net = pkg.Microcircuit(cfg, seed=5, stream=torch.cuda.current_stream())
+    kw = {"n_part": n_part} if n_part else {}
+    net = pkg.Microcircuit(cfg, seed=5, stream=torch.cuda.current_stream(), **kw)
     start = net.save_state()
     scales = torch.tensor(alpha0, dtype=torch.float64, requires_grad=True)
     nu = torch.tensor(nu0, dtype=torch.float64, requires_grad=True)

@@ -212,6 +212,31 @@ def test_deliver_matches_oracle(cfg01, onet01, n_spikes, tiling):
     np.testing.assert_array_equal(net.ring(), ref.astype(np.int32))
 
 
+@pytest.mark.parametrize("tiling", [0, 1, 2, 3, 4, 5])
+def test_deliver_adds_to_a_live_ring(cfg01, onet01, tiling):
+    """Delivery into a ring that already holds the inputs of 20 steps, twice
+    in a row at different steps: the ring changes by exactly the oracle's
+    delivery (int32 arithmetic modulo 2^32), and the event counter by the
+    rows' lengths."""
+    net = gpu_net(cfg01)
+    net.step(20)
+    net.sync()
+    rp, _, _, _ = onet01.export()
+    for k, (m, t) in enumerate([(4000, 20), (1500, 23)]):
+        before = net.ring().astype(np.int64)
+        ev0 = net.counters()["events"]
+        spikes = workload.random_spike_list(net.n, m, seed=500 + k).astype(np.int32)
+        d = torch.from_numpy(spikes).cuda()
+        net.deliver(d.data_ptr(), spikes.size, t, tiling)
+        net.sync()
+        delta = (net.ring().astype(np.int64) - before) % 2**32
+        ref = onet01.deliver(spikes, t).astype(np.int64) % 2**32
+        np.testing.assert_array_equal(delta, ref)
+        if tiling == 3:
+            rl = np.diff(rp.astype(np.int64))
+            assert net.counters()["events"] - ev0 == int(rl[spikes].sum())
+
+
 def test_deliver_partition_tilings_with_global_ring(cfg01, onet01):
     """Two partitions of 3,859 neurons: the ring does not fit in shared memory
     and the partition tiling accumulates into global memory."""
