@@ -18,11 +18,13 @@
 // alone writes the outputs (the lI ring, the nu sums and, at the end, the
 // adjoint state).
 //
-// A lane takes one source: its run is summed in order, so every sum has a
-// fixed order.  Sources are sorted by run length and packed 32 to a lane
-// group, their entries stored column by column (entry k of lane l at
-// k * 32 + l), so that a warp walks 32 runs of similar length with
-// conflict-free entry loads.  A run shorter than its group's longest is padded
+// A lane takes one source, or one chunk of a source's run when the run is
+// longer than kApChunk entries (up to kApMaxChunks chunks in consecutive
+// lanes, added in chunk order by the first): every sum has a fixed order.
+// Sources are sorted by chunk length, dealt to the groups in snake order and
+// packed 32 lanes to a lane group, their entries stored column by column
+// (entry k of lane l at k * 32 + l), so that a warp walks 32 runs of similar
+// length with conflict-free entry loads.  A run shorter than its group's longest is padded
 // with entries of weight zero (exact: x + 0 * lI = x for the finite lI), so
 // the walk has no per-entry test and its loads pipeline.  Lane groups are
 // dealt to the warps longest first, each to the least loaded warp.
@@ -39,9 +41,12 @@ constexpr int kApWarps = kApThreads / 32;
 constexpr uint32_t kApNone = 0xffffffffu;
 constexpr uint32_t kApLocBits = 13;          // local target < 2^13
 constexpr uint32_t kApWBits = 19;            // weight index << 19 | delay << 13 | local
+constexpr uint32_t kApChunk = 32;           // entries per lane before a run is split
+constexpr uint32_t kApMaxChunks = 4;         // lanes one source's run is split over
 constexpr int kApPre = 4;                    // neurons per thread in the membrane phase (ncmax <= 2048)
 constexpr int kApHeader = 8;                 // n_lg, nc, p_lo, span, e_off, 0, 0, 0
-// header, then lenmax[n_lg], ebase[n_lg], src[32 n_lg], len[32 n_lg],
+// header, then lenmax[n_lg], ebase[n_lg], src[32 n_lg], chunks[32 n_lg] (m on
+// a source's first lane, else 0),
 // warp_first[kApWarps + 1], lg_order[n_lg], then the entries at e_off
 
 __global__ void __launch_bounds__(kApThreads, 1)
@@ -146,8 +151,29 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
                     for (int kk = 0; kk < kMaxPop; ++kk) pa[kk] = __fadd_rn(pa[kk], kk == (int)pr ? v : 0.f);
                 }
             }
-            if (j != kApNone) {
-                __stcg(&pds[(size_t)c * n + j], acc);
+            // the chunks of a source sit in consecutive lanes; its first lane
+            // (m > 0) adds them in chunk order
+            const uint32_t m = lens[L * 32 + lane];
+            float tot = acc;
+#pragma unroll
+            for (uint32_t r = 1; r < kApMaxChunks; ++r) {
+                const float v = __shfl_down_sync(0xffffffffu, acc, r);
+                if (r < m) tot = __fadd_rn(tot, v);
+            }
+            if (__any_sync(0xffffffffu, spk)) {
+#pragma unroll
+                for (int kk = 0; kk < kMaxPop; ++kk) {
+                    float t2 = pa[kk];
+#pragma unroll
+                    for (uint32_t r = 1; r < kApMaxChunks; ++r) {
+                        const float v = __shfl_down_sync(0xffffffffu, pa[kk], r);
+                        if (r < m) t2 = __fadd_rn(t2, v);
+                    }
+                    pa[kk] = t2;
+                }
+            }
+            if (m > 0u) {
+                __stcg(&pds[(size_t)c * n + j], tot);
                 if (spk) {
                     double* ga = p.gAc + ((size_t)c * n + j) * kMaxPop;
 #pragma unroll
@@ -263,20 +289,44 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
             const uint32_t* sg = seg.data() + (size_t)j * (n_part + 1) + c;
             return sg[1] - sg[0];
         };
-        // source groups with equal work (entries + 1 per source)
-        unsigned long long total = 0;
-        for (int32_t j = 0; j < n; ++j) total += run_len(j) + 1ull;
-        int32_t j0 = 0;
-        unsigned long long acc = 0;
+        // a source is one unit of m <= kApMaxChunks lanes: its run in chunks
+        // of at most kApChunk entries (as equal as possible), one per lane
+        struct Unit {
+            int32_t j;
+            uint32_t m, clen;                 // chunks, entries of the longest chunk
+        };
+        std::vector<Unit> units(n);
+        for (int32_t j = 0; j < n; ++j) {
+            const uint32_t len = run_len(j);
+            const uint32_t m = std::min<uint32_t>(kApMaxChunks, std::max<uint32_t>(1u, (len + kApChunk - 1) / kApChunk));
+            units[j] = Unit{j, m, (len + m - 1) / m};
+        }
+        // longest chunks first, dealt to the G groups in snake order (0 .. G-1,
+        // G-1 .. 0, ...): every group gets the same mix of chunk lengths
+        std::stable_sort(units.begin(), units.end(), [](const Unit& x, const Unit& y) { return x.clen > y.clen; });
+        std::vector<std::vector<Unit>> groups(G);
+        for (int32_t k = 0; k < n; ++k) {
+            const int r = k % G, lap = k / G;
+            groups[(lap & 1) ? G - 1 - r : r].push_back(units[k]);
+        }
         for (int g = 0; g < G; ++g) {
-            int32_t j1 = j0;
-            const unsigned long long goal = total * (unsigned long long)(g + 1) / G;
-            while (j1 < n && (g == G - 1 || acc + run_len(j1) + 1ull <= goal)) acc += run_len(j1++) + 1ull;
-            std::vector<int32_t> srcs;
-            for (int32_t j = j0; j < j1; ++j) srcs.push_back(j);
-            std::stable_sort(srcs.begin(), srcs.end(),
-                             [&](int32_t a, int32_t b) { return run_len(a) > run_len(b); });
-            const uint32_t n_lg = (uint32_t)((srcs.size() + 31) / 32);
+            // lanes: source, chunk, entries; a unit never straddles two lane groups
+            struct Lane {
+                int32_t j;
+                uint32_t m, k0, len;          // m on the unit's first lane only
+            };
+            std::vector<Lane> lanes;
+            for (const Unit& u : groups[g]) {
+                if (lanes.size() % 32 + u.m > 32)
+                    while (lanes.size() % 32) lanes.push_back(Lane{-1, 0u, 0u, 0u});
+                const uint32_t len = run_len(u.j);
+                for (uint32_t q = 0; q < u.m; ++q) {
+                    const uint32_t k0 = std::min(len, q * u.clen);
+                    lanes.push_back(Lane{u.j, q == 0 ? u.m : 0u, k0, std::min(len, k0 + u.clen) - k0});
+                }
+            }
+            const uint32_t n_lg = (uint32_t)((lanes.size() + 31) / 32);
+            while (lanes.size() < (size_t)n_lg * 32) lanes.push_back(Lane{-1, 0u, 0u, 0u});
             const size_t o_wf = kApHeader + 2 * (size_t)n_lg + 64 * (size_t)n_lg;
             std::vector<uint32_t> head(o_wf + kApWarps + 1 + n_lg, 0u);
             head[0] = n_lg;
@@ -285,16 +335,16 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
             head[3] = (uint32_t)span;
             std::vector<uint32_t> ents;
             for (uint32_t L = 0; L < n_lg; ++L) {
-                const uint32_t lm = run_len(srcs[L * 32]);
+                uint32_t lm = 0;
+                for (uint32_t l = 0; l < 32; ++l) lm = std::max(lm, lanes[L * 32 + l].len);
                 head[kApHeader + L] = lm;
                 head[kApHeader + n_lg + L] = (uint32_t)ents.size();
                 for (uint32_t k = 0; k < lm; ++k)
                     for (uint32_t l = 0; l < 32; ++l) {
-                        const size_t si = (size_t)L * 32 + l;
+                        const Lane& ln = lanes[L * 32 + l];
                         uint32_t e = e_pad;
-                        if (si < srcs.size() && k < run_len(srcs[si])) {
-                            const int32_t j = srcs[si];
-                            const uint32_t pe = pre[seg[(size_t)j * (n_part + 1) + c] + k];
+                        if (ln.j >= 0 && k < ln.len) {
+                            const uint32_t pe = pre[seg[(size_t)ln.j * (n_part + 1) + c] + ln.k0 + k];
                             const uint32_t off_e = pe & kPreOffMask;
                             const uint32_t d = off_e / (uint32_t)ncmax, loc = off_e % (uint32_t)ncmax;
                             const uint32_t wi = (pe >> kPreOffBits) - (uint32_t)p_lo * kMaxPop * kWCodes;
@@ -308,9 +358,8 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
                     }
             }
             for (uint32_t l = 0; l < 32 * n_lg; ++l) {
-                const bool ok = l < srcs.size();
-                head[kApHeader + 2 * n_lg + l] = ok ? (uint32_t)srcs[l] : kApNone;
-                head[kApHeader + 2 * n_lg + 32 * n_lg + l] = ok ? run_len(srcs[l]) : 0u;
+                head[kApHeader + 2 * n_lg + l] = lanes[l].j >= 0 ? (uint32_t)lanes[l].j : kApNone;
+                head[kApHeader + 2 * n_lg + 32 * n_lg + l] = lanes[l].m;
             }
             // lane groups to warps, longest first, each to the least loaded warp
             std::vector<std::vector<uint32_t>> per_warp(kApWarps);
@@ -333,7 +382,6 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
             img.insert(img.end(), head.begin(), head.end());
             off.push_back((uint32_t)img.size());
             img_max = std::max(img_max, head.size());
-            j0 = j1;
         }
     }
     const size_t smem = img_max * 4 + (size_t)R * ncmax * 4 + (size_t)2 * (span_max * kMaxPop * kWCodes + 4) * 4 +

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256) k_adj_predecode(int32_t n, int32_t n_pop,
 }
 
 // dL/dalpha_pq = sum over j in q of gA[j][p]; dL/dnu = sum_j gN[j] dnu[pop j].
-// One CTA, every output reduced in the same fixed order.
+// One CTA per output (64 scales, then nu), each reduced in a fixed order.
 __global__ void __launch_bounds__(512) k_grad_reduce(int32_t n, int32_t n_pop,
                                                      const int32_t* __restrict__ pop_start_dev,
                                                      const double* __restrict__ gA,
@@ -327,7 +327,8 @@ __global__ void __launch_bounds__(512) k_grad_reduce(int32_t n, int32_t n_pop,
     const int tid = threadIdx.x;
     if (tid <= kMaxPop) ps[tid] = pop_start_dev[tid];
     __syncthreads();
-    for (int o = 0; o <= kMaxPop * kMaxPop; ++o) {
+    {
+        const int o = blockIdx.x;
         double v = 0.0;
         if (o < kMaxPop * kMaxPop) {
             const int p = o / kMaxPop, q = o % kMaxPop;
@@ -343,7 +344,6 @@ __global__ void __launch_bounds__(512) k_grad_reduce(int32_t n, int32_t n_pop,
             __syncthreads();
         }
         if (tid == 0) out[o] = red[0];
-        __syncthreads();
     }
 }
 
@@ -708,7 +708,7 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
     }
     if (g->part)
         GCK(launch_adjoint_part_fold(n, P, net->n_pop, net->d_part_lo, g->pop_start, g->gAc, g->gA, s));
-    k_grad_reduce<<<1, 512, 0, s>>>(n, net->n_pop, g->pop_start, g->gA, g->gN, g->out + kMaxPop * kMaxPop + 1,
+    k_grad_reduce<<<kMaxPop * kMaxPop + 1, 512, 0, s>>>(n, net->n_pop, g->pop_start, g->gA, g->gN, g->out + kMaxPop * kMaxPop + 1,
                                      g->out);
     GCK(cudaGetLastError());
     // back to the state after the forward, with the caller's counters
