@@ -18,8 +18,10 @@
 // and C(t) (I_t = P11 I_{t-1} + ring[t] + background).  A(t + 1) needs only
 // I_t, and C(t) needs the deliveries of step t - 1, so one grid barrier per
 // step suffices:
-//     A(t0);  for t: { barrier; D(t); C(t); A(t + 1) }
-// D(t) writes slots t + 1 .. t + R - 1 (mod R) while C(t) reads slot t; the lists and
+//     A(t0);  for t: { barrier; C(t); A(t + 1); D(t) }
+// C(t) and A(t + 1) come first: they need only slot t, filled by D(t - 1)
+// before the barrier, and run while no CTA has atomics in flight; D(t) then
+// writes slots t + 1 .. t + R - 1 (mod R), never slot t.  The lists and
 // their counters rotate over 2 and 4 step parities, so each buffer is reset
 // or rewritten only after the barrier that ends its last reader's phase.
 // Every result equals the single-network path bit for bit (same fp32
@@ -412,25 +414,6 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ 
         // counters of step t + 2: last read in D(t - 2), next written in A(t + 2)
         if (blockIdx.x == 0 && tid < kTilings) p.cnt[(uint32_t)((t + 2) & 3) * kTilings + tid] = 0u;
 
-        // ---- D(t): spikes of step t ----
-        {
-            const uint32_t par4 = (uint32_t)(t & 3), par2 = (uint32_t)(t & 1);
-            const uint32_t nw = __ldcg(&p.cnt[par4 * kTilings + 0]);
-            const uint32_t nb = __ldcg(&p.cnt[par4 * kTilings + 1]);
-            const uint32_t nf = __ldcg(&p.cnt[par4 * kTilings + 2]);
-            const uint32_t* lw = p.list + ((size_t)par2 * kTilings + 0) * ntot;
-            const uint32_t* lb = p.list + ((size_t)par2 * kTilings + 1) * ntot;
-            const uint32_t* lf = p.list + ((size_t)par2 * kTilings + 2) * ntot;
-            if (nf) deliver_flat(p, s_goff, F, lf, nf, tD, true);
-            // warp w of CTA b takes spikes w * grid + b, spreading them over SMs
-            for (uint32_t k = (uint32_t)(tid >> 5) * gridDim.x + blockIdx.x; k < nw;
-                 k += (uint32_t)kBWarps * gridDim.x)
-                deliver_row<kWarpUnroll>(p, s_goff, (int32_t)__ldcg(&lw[k]), tD, lane, 32, true);
-            // CTA rows start from the last CTA, away from the first warp rows
-            for (uint32_t k = gridDim.x - 1u - blockIdx.x; k < nb; k += gridDim.x)
-                deliver_row<kBlockUnroll>(p, s_goff, (int32_t)__ldcg(&lb[k]), tD, tid, kBThreads, true);
-        }
-
         // ---- C(t): ring slot t, background, synaptic current ----
         {
             int32_t* rs = p.ring + (size_t)tD * ntot;
@@ -477,6 +460,24 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ 
         }
         // ---- A(t + 1) ----
         if (s + 1 < n) phase_a(t + 1);
+        // ---- D(t): spikes of step t ----
+        {
+            const uint32_t par4 = (uint32_t)(t & 3), par2 = (uint32_t)(t & 1);
+            const uint32_t nw = __ldcg(&p.cnt[par4 * kTilings + 0]);
+            const uint32_t nb = __ldcg(&p.cnt[par4 * kTilings + 1]);
+            const uint32_t nf = __ldcg(&p.cnt[par4 * kTilings + 2]);
+            const uint32_t* lw = p.list + ((size_t)par2 * kTilings + 0) * ntot;
+            const uint32_t* lb = p.list + ((size_t)par2 * kTilings + 1) * ntot;
+            const uint32_t* lf = p.list + ((size_t)par2 * kTilings + 2) * ntot;
+            if (nf) deliver_flat(p, s_goff, F, lf, nf, tD, true);
+            // warp w of CTA b takes spikes w * grid + b, spreading them over SMs
+            for (uint32_t k = (uint32_t)(tid >> 5) * gridDim.x + blockIdx.x; k < nw;
+                 k += (uint32_t)kBWarps * gridDim.x)
+                deliver_row<kWarpUnroll>(p, s_goff, (int32_t)__ldcg(&lw[k]), tD, lane, 32, true);
+            // CTA rows start from the last CTA, away from the first warp rows
+            for (uint32_t k = gridDim.x - 1u - blockIdx.x; k < nb; k += gridDim.x)
+                deliver_row<kBlockUnroll>(p, s_goff, (int32_t)__ldcg(&lb[k]), tD, tid, kBThreads, true);
+        }
     }
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
