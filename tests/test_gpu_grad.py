@@ -209,6 +209,34 @@ def test_surrogate_gradient_short_horizon(t_ref, steps, n_part):
     assert_gradient_close(scales.grad.numpy(), nu.grad.item(), ref)
 
 
+@pytest.mark.parametrize("variant", ["dc_input", "three_partitions"])
+def test_surrogate_gradient_variants(variant):
+    """The adjoint against the oracle's on the 2 % network (seed 5, 100 steps)
+    with DC input in place of the Poisson drive (no nu gradient), and with
+    three partitions of uneven population mix."""
+    cfg = workload.microcircuit(0.02, seed=5)
+    kw = {}
+    if variant == "dc_input":
+        cfg = workload.dc_variant(cfg)
+    else:
+        kw["n_part"] = 3
+    steps = 100
+    targets = workload.target_rates()
+    alpha0, nu0 = _alpha(7), float(cfg["nu_bg"])
+    ref = oracle.hard_gradient(cfg, alpha0, nu0, steps, targets, seed=5)
+    net = pkg.Microcircuit(cfg, seed=5, stream=torch.cuda.current_stream(), **kw)
+    start = net.save_state()
+    scales = torch.tensor(alpha0, dtype=torch.float64, requires_grad=True)
+    nu = torch.tensor(nu0, dtype=torch.float64, requires_grad=True)
+    rates = microcircuit_rates(scales, nu, net, steps, 30, start)
+    np.testing.assert_allclose(rates.detach().numpy(), ref["rates"], rtol=1e-12)
+    loss = ((rates - torch.as_tensor(targets)) ** 2).mean()
+    loss.backward()
+    assert_gradient_close(scales.grad.numpy(), nu.grad.item(), ref)
+    if variant == "dc_input":
+        assert nu.grad.item() == 0.0 and ref["g_nu"] == 0.0
+
+
 def test_gradient_independent_of_checkpoint_spacing(config3):
     cfg, targets, alpha0, nu0, _ = config3
     net = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
