@@ -380,7 +380,10 @@ def extra_grad(pkg, workload, torch, stream, reps=3):
             "note": "the adjoint grows ~e^0.039 per step through the chaotic dynamics: over "
                     "200 ms max|g| reaches ~4e31, so the gradient's value is dominated by that "
                     "growth; the figure times the computation, not its usefulness for training",
-            "gpu_launches": 3 * ((n_steps + every - 1) // every) + 1,
+            # per gradient: one k_step per checkpoint segment (forward, with the
+            # trajectory recorded), one k_adjoint_part per segment, the fold and
+            # the reduction
+            "gpu_launches": 2 * ((n_steps + every - 1) // every) + 2,
             "clocks": clk.summary(),
             "config": {"workload": "10%% microcircuit (7,717 neurons), %d time steps, checkpoints "
                                    "every %d steps, gradient w.r.t. 64 projection scales and nu"
@@ -920,9 +923,10 @@ def run_grad(args):
                    "l2": "not flushed; wall-clock per gradient including host marshalling"},
         "loss": loss, "grad_abs_max": float(gs.abs().max()), "grad_nu": float(gn),
         "clocks": clk.summary(),
-        # per gradient: one k_step per checkpoint segment forward, k_step +
-        # k_adjoint per segment backward, and the final k_grad_reduce
-        "gpu_launches": args.steps * (3 * ((n_steps + every - 1) // every) + 1),
+        # per gradient: one k_step per checkpoint segment (forward, with the
+        # trajectory recorded), one k_adjoint_part per segment, the fold and
+        # the reduction
+        "gpu_launches": args.steps * (2 * ((n_steps + every - 1) // every) + 2),
     }
     print(json.dumps(line), flush=True)
 

@@ -379,9 +379,9 @@ int snn_set_params(snn_net* net, const double* scales, double nu_bg);
  * return the population rates (Hz) over those steps in rates_host[8].
  * snn_grad_backward -- given g_rate[8] = dL/d rate_p of any loss of those
  * rates, return dL/d alpha (g_alpha[p*8 + q]) and dL/d nu_bg (*g_nu) by
- * backpropagation through time: each segment is restored from its
- * checkpoint, re-run with its trajectory recorded, and differentiated in
- * reverse.  Spike derivative: the fast-sigmoid surrogate 1/(1+10|u-theta|)^2
+ * backpropagation through time: each segment's trajectory (recorded by the
+ * forward when it fits the trace budget, see snn_grad_set_trace_budget, else
+ * recomputed from the segment's checkpoint) is differentiated in reverse.  Spike derivative: the fast-sigmoid surrogate 1/(1+10|u-theta|)^2
  * per mV; reset and refractory are held fixed; the weight rounding and the
  * Poisson count pass their derivative straight through (d w/d alpha = the
  * unrounded base weight, d k/d nu = K_ext dt).  fp32 adjoint state, double
@@ -393,6 +393,18 @@ int snn_set_params(snn_net* net, const double* scales, double nu_bg);
  */
 int snn_grad_forward(snn_net* net, int64_t n_steps, int32_t ckpt_every, double* rates_host);
 int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, double* g_nu);
+
+/*
+ * snn_grad_set_trace_budget -- largest trajectory of a whole snn_grad_forward
+ * kept on the device, in bytes (5 per neuron-step: u and the spike/update
+ * flags; default 4 GiB, and never more than a quarter of the free device
+ * memory at the forward).  A forward whose trajectory fits records it as it
+ * runs, and the backward then re-runs nothing; otherwise the backward re-runs
+ * each checkpoint segment to record it.  0 always re-runs.  The gradient is
+ * the same bit for bit either way.  Applies from the next forward.
+ * Errors: SNN_ERR_INVALID (null net, negative bytes).
+ */
+int snn_grad_set_trace_budget(snn_net* net, int64_t bytes);
 
 /*
  * ---------------------------------------------------------------------------

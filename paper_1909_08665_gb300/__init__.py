@@ -107,6 +107,7 @@ EXPORTED = ["snn_create", "snn_create_from_rows", "snn_step", "snn_sync", "snn_r
             "snn_record_step_counts",
             "snn_set_realtime", "snn_realtime_stats", "snn_save_state",
             "snn_load_state", "snn_set_params", "snn_grad_forward", "snn_grad_backward",
+            "snn_grad_set_trace_budget",
             "snn_batch_create",
             "snn_batch_step", "snn_batch_sync", "snn_batch_read_spikes", "snn_batch_read_state",
             "snn_batch_counters", "snn_batch_get_info", "snn_batch_set_tiling",
@@ -151,6 +152,7 @@ def lib():
         L.snn_set_params.argtypes = [vp, P(C.c_double), C.c_double]
         L.snn_grad_forward.argtypes = [vp, C.c_int64, C.c_int32, P(C.c_double)]
         L.snn_grad_backward.argtypes = [vp, P(C.c_double), P(C.c_double), P(C.c_double)]
+        L.snn_grad_set_trace_budget.argtypes = [vp, C.c_int64]
         L.snn_batch_create.argtypes = [P(SnnConfig), P(C.c_uint64), C.c_int32, P(SnnOptions),
                                        vp, P(vp)]
         L.snn_batch_step.argtypes = [vp, C.c_int64]
@@ -362,6 +364,10 @@ class Microcircuit:
         r = np.zeros(MAX_POP, np.float64)
         _check(lib().snn_grad_forward(self._h, int(n_steps), int(ckpt_every), _ptr(r, C.c_double)))
         return r[:len(self.cfg["pop_sizes"])]
+
+    def set_grad_trace_budget(self, n_bytes: int):
+        """Largest whole-forward trajectory kept for the backward (bytes)."""
+        _check(lib().snn_grad_set_trace_budget(self._h, int(n_bytes)))
 
     def grad_backward(self, g_rate):
         """dL/dalpha [8][8] and dL/dnu for g_rate = dL/d(rates)."""

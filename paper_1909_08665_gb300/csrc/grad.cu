@@ -24,7 +24,10 @@
 // restores each segment's checkpoint, re-runs the segment with the step
 // kernel recording u (before reset) and the spike / update flags, then runs
 // the adjoint over the segment in one persistent cooperative kernel (one
-// grid barrier per step).  lI of the last 64 steps lives in an adjoint ring
+// grid barrier per step).  When the trace of the whole forward (5 bytes per
+// neuron-step) fits the trace budget (4 GiB by default) and a quarter of the
+// free device memory, the forward records it directly and the backward
+// re-runs nothing.  lI of the last 64 steps lives in an adjoint ring
 // [64][n]; per-neuron sums are double and every reduction has a fixed order,
 // so results are deterministic.
 #include <algorithm>
@@ -48,6 +51,8 @@ struct snn_grad {
     size_t ckpt_bytes = 0;
     size_t ckpt_cap = 0;            // checkpoints the buffer holds
     int32_t tr_cap = 0;             // steps the trace buffers hold
+    bool full_trace = false;        // the forward recorded every step: no recomputation
+    int64_t trace_budget = (int64_t)4 << 30;   // bytes of a whole forward's trace
     uint8_t* ckpt = nullptr;        // [n_seg + 1][u | I | refr | ring]
     float* tr_u = nullptr;          // [seg][n]
     uint8_t* tr_f = nullptr;        // [seg][n]
@@ -462,20 +467,34 @@ int snn_grad_forward(snn_net* net, int64_t n_steps, int32_t ckpt_every, double* 
         GCALL(galloc(&g->ckpt, g->ckpt_bytes * ((size_t)n_seg + 1), "gradient checkpoints"));
         g->ckpt_cap = (size_t)n_seg + 1;
     }
-    if (g->tr_u && g->tr_cap < seg) {
+    // the trace of every step when it fits, else of one segment
+    size_t free_b = 0, total_b = 0;
+    GCK(cudaMemGetInfo(&free_b, &total_b));
+    const size_t full_bytes = (size_t)n_steps * n * (sizeof(float) + 1);
+    const bool full = (int64_t)full_bytes <= g->trace_budget && full_bytes <= free_b / 4;
+    const int32_t tr_steps = full ? (int32_t)n_steps : seg;
+    if (g->tr_u && g->tr_cap < tr_steps) {
         cudaFree(g->tr_u);
         cudaFree(g->tr_f);
         g->tr_u = nullptr;
         g->tr_f = nullptr;
+        g->tr_cap = 0;
     }
-    GCALL(galloc(&g->tr_u, (size_t)seg * n, "gradient trace"));
-    GCALL(galloc(&g->tr_f, (size_t)seg * n, "gradient trace"));
-    g->tr_cap = std::max(g->tr_cap, seg);
+    GCALL(galloc(&g->tr_u, (size_t)tr_steps * n, "gradient trace"));
+    GCALL(galloc(&g->tr_f, (size_t)tr_steps * n, "gradient trace"));
+    g->tr_cap = std::max(g->tr_cap, tr_steps);
+    g->full_trace = full;
     cudaStream_t s = net->stream;
     GCK(cudaMemsetAsync(net->d_pop_spikes, 0, sizeof(unsigned long long) * kMaxPop, s));
     StepParams sp;
     fill_step_params(net, &sp);
     const int64_t t0 = net->step;
+    if (full) {
+        sp.tr_u = g->tr_u;
+        sp.tr_f = g->tr_f;
+        sp.tr_t0 = t0;
+        sp.tr_len = (int32_t)n_steps;
+    }
     for (int32_t c = 0; c < n_seg; ++c) {
         GCK(save_ckpt(net, g->ckpt + (size_t)c * g->ckpt_bytes));
         const int64_t len = std::min<int64_t>(seg, n_steps - (int64_t)c * seg);
@@ -499,6 +518,13 @@ int snn_grad_forward(snn_net* net, int64_t n_steps, int32_t ckpt_every, double* 
     g->seg = seg;
     g->n_seg = n_seg;
     g->ready = true;
+    return SNN_OK;
+}
+
+int snn_grad_set_trace_budget(snn_net* net, int64_t bytes) {
+    if (!net || bytes < 0) return set_error(SNN_ERR_INVALID, "bad arguments");
+    if (!net->grad) net->grad = new snn_grad();
+    net->grad->trace_budget = bytes;
     return SNN_OK;
 }
 
@@ -652,10 +678,15 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
     for (int32_t c = g->n_seg - 1; c >= 0; --c) {
         const int64_t t0 = g->t_start + (int64_t)c * g->seg;
         const int32_t len = (int32_t)std::min<int64_t>(g->seg, g->n_steps - (int64_t)c * g->seg);
-        GCK(load_ckpt(net, g->ckpt + (size_t)c * g->ckpt_bytes));
-        sp.tr_t0 = t0;
-        sp.tr_len = len;
-        GCK(net_launch(net, sp, t0, len));
+        // this segment's trace rows: recorded by the forward, or recomputed
+        // from its checkpoint
+        const size_t tr_off = g->full_trace ? (size_t)c * g->seg * n : 0;
+        if (!g->full_trace) {
+            GCK(load_ckpt(net, g->ckpt + (size_t)c * g->ckpt_bytes));
+            sp.tr_t0 = t0;
+            sp.tr_len = len;
+            GCK(net_launch(net, sp, t0, len));
+        }
         GCK(cudaMemsetAsync(g->sync, 0, sizeof(uint32_t), s));
         if (g->part) {
             AdjPartParams pp;
@@ -676,8 +707,8 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
             pp.part_lo = net->d_part_lo;
             pp.wtab = net->d_wtab;
             pp.wbase = g->wbase;
-            pp.tr_u = g->tr_u;
-            pp.tr_f = g->tr_f;
+            pp.tr_u = g->tr_u + tr_off;
+            pp.tr_f = g->tr_f + tr_off;
             pp.lu = g->lu;
             pp.lI = g->lI;
             pp.lring = g->lring;
@@ -693,6 +724,8 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
         }
         ap.t_first = t0;
         ap.len = len;
+        ap.tr_u = g->tr_u + tr_off;
+        ap.tr_f = g->tr_f + tr_off;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(kAdjThreads);

@@ -238,11 +238,15 @@ def test_surrogate_gradient_variants(variant):
 
 
 def test_gradient_independent_of_checkpoint_spacing(config3):
+    """The same gradient bit for bit for every checkpoint spacing, whether the
+    forward keeps the whole trajectory or the backward re-runs each segment
+    from its checkpoint (trace budget 0)."""
     cfg, targets, alpha0, nu0, _ = config3
     net = pkg.Microcircuit(cfg, stream=torch.cuda.current_stream())
     start = net.save_state()
     out = []
-    for every in (100, 37, 2000):
+    for every, budget in ((100, 4 << 30), (37, 4 << 30), (2000, 4 << 30), (100, 0), (37, 0)):
+        net.set_grad_trace_budget(budget)
         net.load_state(start)
         net.set_params(alpha0, nu0)
         r = net.grad_forward(2000, every)
