@@ -97,8 +97,12 @@ def test_raster_and_state_bit_exact(cfg01, onet01, n_part):
     assert not oc["saturated"]
 
 
-def test_launch_boundaries_do_not_change_results(cfg01, onet01):
-    net = gpu_net(cfg01)
+@pytest.mark.parametrize("n_part", [0, 2])
+def test_launch_boundaries_do_not_change_results(cfg01, onet01, n_part):
+    """Launches of 0 to 371 steps: results equal one long run, with the ring
+    in shared memory (default partitions) and in global memory (two
+    partitions of 3,859 neurons)."""
+    net = gpu_net(cfg01, n_part=n_part)
     sim = oracle.Simulation(onet01)
     for n in (1, 1, 2, 3, 5, 117, 0, 371):
         net.step(n)
