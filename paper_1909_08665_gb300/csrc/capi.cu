@@ -405,6 +405,9 @@ int build_rows(snn_net* net) {
 }
 
 int build_generated(snn_net* net) {
+    net->max_delay = 1;
+    for (int q = 0; q < net->n_pop; ++q)
+        for (int k = 0; k < kDCodes; ++k) net->max_delay = std::max<int32_t>(net->max_delay, net->dtab[q * kDCodes + k]);
     CALL(build_rows(net));
     return finish_network(net);
 }
@@ -415,6 +418,7 @@ int build_from_rows(snn_net* net, const uint64_t* row_ptr, const uint32_t* words
     const int n = net->n, P = net->P;
     if (!row_ptr || !words || !wtab) return fail(SNN_ERR_INVALID, "rows, words and wtab are required");
     if (row_ptr[0] != 0) return fail(SNN_ERR_INVALID, "row_ptr[0] must be 0");
+    net->max_delay = 1;
     for (int j = 0; j < n; ++j) {
         if (row_ptr[j + 1] < row_ptr[j]) return fail(SNN_ERR_INVALID, "row_ptr must not decrease");
         uint32_t prev = 0;
@@ -423,6 +427,7 @@ int build_from_rows(snn_net* net, const uint64_t* row_ptr, const uint32_t* words
             const uint32_t d = (words[e] >> kTgtBits) & 63u;
             if ((int)t >= n) return fail(SNN_ERR_INVALID, "target index out of range");
             if (d < 1) return fail(SNN_ERR_INVALID, "delay must be 1..63 steps");
+            net->max_delay = std::max<int32_t>(net->max_delay, (int32_t)d);
             if (e > row_ptr[j] && t < prev) return fail(SNN_ERR_INVALID, "targets must ascend within a row");
             prev = t;
         }
@@ -940,6 +945,7 @@ int snn_deliver(snn_net* net, const uint32_t* spikes_dev, int32_t n_spikes, int6
     dp.counters = net->d_counters;
     dp.status = net->d_sync + 4;
     dp.pre = net->d_pre;
+    dp.max_delay = net->max_delay;
     if (tiling == 5) {
         int dev = 0, optin = 0;
         CK(cudaGetDevice(&dev));

@@ -1,8 +1,12 @@
 // deliver_words.cu -- stand-alone delivery of one long spike list (Sec. 3.1.2:
 // row fetch, word decode, ring-buffer add), partition by partition.
 //
-// CTA c owns partition c's ring slice (in shared memory when it fits) and
-// reads, for every spike j of the list, exactly the entries of row j that
+// CTA c sums the list's input to partition c in shared memory when it fits --
+// only the ring slots the list can reach, t + 1 .. t + D (D the longest delay
+// of the network), zeroed at the start, so nothing is read in before the adds
+// -- and adds the non-zero sums into the ring slice at the end; otherwise it
+// adds straight into the ring slice in global memory.  For every spike j of
+// the list it reads exactly the entries of row j that
 // target partition c: the run [seg[j][c], seg[j][c + 1]) of the row, which is
 // contiguous because rows are sorted by target.  That is the algorithmic 4
 // bytes per synaptic event and no more, and every add is a shared-memory
@@ -73,14 +77,15 @@ struct WordsSmem {
 };
 
 // dynamic shared memory: weight table [p][q][code], per-warp segment offsets
-// and start bitmaps, then (optionally) the ring slice [slot][ncmax]
-__host__ __device__ WordsSmem words_smem(int ncmax, bool smem_ring) {
+// and start bitmaps, then (optionally) the sums [delay - 1][ncmax] of delays
+// 1 .. depth (rounded up to whole 16-byte vectors)
+__host__ __device__ WordsSmem words_smem(int ncmax, bool smem_ring, int depth) {
     WordsSmem L;
     L.off_wt = 0;
     L.off_info = L.off_wt + (size_t)kMaxPop * kMaxPop * kWCodes * 4;
     L.off_bm = L.off_info + (size_t)kWWarps * kRoundSpikes * 4;
     L.off_ring = L.off_bm + (size_t)kWWarps * kBmWords * 4;
-    L.total = L.off_ring + (smem_ring ? (size_t)kRing * ncmax * 4 : 0);
+    L.total = L.off_ring + (smem_ring ? ((size_t)depth * ncmax + 3) / 4 * 16 : 0);
     return L;
 }
 
@@ -89,7 +94,8 @@ __global__ void __launch_bounds__(kWThreads, 1)
 k_deliver_words(const __grid_constant__ DeliverParams dp) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_next_round;
-    const WordsSmem L = words_smem(dp.ncmax, SMEM_RING);
+    const int depth = dp.max_delay;
+    const WordsSmem L = words_smem(dp.ncmax, SMEM_RING, depth);
     int32_t* s_wt = reinterpret_cast<int32_t*>(smem + L.off_wt);
     const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t* info = reinterpret_cast<uint32_t*>(smem + L.off_info) + warp * kRoundSpikes;
@@ -99,10 +105,10 @@ k_deliver_words(const __grid_constant__ DeliverParams dp) {
     int32_t* ring = SMEM_RING ? reinterpret_cast<int32_t*>(smem + L.off_ring) : ring_g;
 
     for (int k = tid; k < kMaxPop * kMaxPop * kWCodes; k += kWThreads) s_wt[k] = __ldg(&dp.wtab[k]);
-    if (SMEM_RING) {      // R = 64 ncmax words: a whole number of 16-byte vectors
-        const int4* src = reinterpret_cast<const int4*>(ring_g);
+    const int n_sums = (depth * dp.ncmax + 3) / 4;       // 16-byte vectors of sums
+    if (SMEM_RING) {
         int4* dst = reinterpret_cast<int4*>(ring);
-        for (int k = tid; k < R / 4; k += kWThreads) dst[k] = src[k];
+        for (int k = tid; k < n_sums; k += kWThreads) dst[k] = make_int4(0, 0, 0, 0);
     }
     if (tid == 0) s_next_round = kWWarps;
     __syncthreads();
@@ -227,8 +233,12 @@ k_deliver_words(const __grid_constant__ DeliverParams dp) {
 #pragma unroll
                 for (int u = 0; u < kChunkBatch; ++u) {
                     wt[u] = s_wt[e[u] >> kPreOffBits];           // kNone reads the last entry
-                    a[u] = (e[u] & kPreOffMask) + base_t;        // ring slot t + delay
-                    a[u] = min(a[u], a[u] - (uint32_t)R);        // wrap: a - R is huge when a < R
+                    if (SMEM_RING) {
+                        a[u] = (e[u] & kPreOffMask) - (uint32_t)dp.ncmax;   // sums cell (delay - 1, local)
+                    } else {
+                        a[u] = (e[u] & kPreOffMask) + base_t;    // ring slot t + delay
+                        a[u] = min(a[u], a[u] - (uint32_t)R);    // wrap: a - R is huge when a < R
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < kChunkBatch; ++u) {
@@ -259,9 +269,26 @@ k_deliver_words(const __grid_constant__ DeliverParams dp) {
     }
     __syncthreads();
     if (SMEM_RING) {
-        const int4* src = reinterpret_cast<const int4*>(ring);
-        int4* dst = reinterpret_cast<int4*>(ring_g);
-        for (int k = tid; k < R / 4; k += kWThreads) dst[k] = src[k];
+        // sum of delay d into ring slot t + d (mod 64), zero sums skipped;
+        // kFlush cells per thread have their ring words loaded together
+        constexpr int kFlush = 8;
+        const uint32_t ncm = (uint32_t)dp.ncmax, total = (uint32_t)depth * ncm;
+        for (uint32_t k0 = tid; k0 < total; k0 += kWThreads * kFlush) {
+            int32_t v[kFlush], old[kFlush];
+            uint32_t g[kFlush];
+#pragma unroll
+            for (int u = 0; u < kFlush; ++u) {
+                const uint32_t k = k0 + (uint32_t)u * kWThreads;
+                v[u] = k < total ? ring[k] : 0;
+                const uint32_t d = k / ncm + 1u, l = k - (d - 1u) * ncm;
+                g[u] = (((uint32_t)dp.t + d) & (kRing - 1)) * ncm + l;
+            }
+#pragma unroll
+            for (int u = 0; u < kFlush; ++u) old[u] = v[u] != 0 ? ring_g[g[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < kFlush; ++u)
+                if (v[u] != 0) ring_g[g[u]] = old[u] + v[u];
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) events += __shfl_xor_sync(0xffffffffu, events, o);
@@ -309,8 +336,9 @@ cudaError_t launch_deliver_words(const DeliverParams& dp, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const bool smem_ring = words_smem(dp.ncmax, true).total <= (size_t)optin;
-    const size_t smem = words_smem(dp.ncmax, smem_ring).total;
+    if (dp.max_delay < 1 || dp.max_delay >= kRing) return cudaErrorInvalidValue;
+    const bool smem_ring = words_smem(dp.ncmax, true, dp.max_delay).total <= (size_t)optin;
+    const size_t smem = words_smem(dp.ncmax, smem_ring, dp.max_delay).total;
     if (smem > (size_t)optin) return cudaErrorInvalidConfiguration;
     const void* fn = smem_ring ? reinterpret_cast<const void*>(&k_deliver_words<true>)
                                : reinterpret_cast<const void*>(&k_deliver_words<false>);

@@ -11,6 +11,7 @@ struct snn_grad;
 using snn::kDCodes;
 using snn::kMaxPop;
 using snn::kPoisTable;
+using snn::kRing;
 using snn::kWCodes;
 
 struct snn_net {
@@ -48,6 +49,7 @@ struct snn_net {
     int32_t* d_ring = nullptr;
     int32_t w_span = 1;                    // target populations of the widest partition
     int32_t run_max = 0;                   // longest (row, partition) run
+    int32_t max_delay = kRing - 1;         // longest delay of any synapse (steps)
     std::vector<uint32_t> indeg;           // [n][8] synapses per source population
     long long in_bound = 0;                // largest |input| of one neuron-step (1/256 pA)
     bool sat_check = false;                // in_bound reaches 2^31: count wrap-arounds

@@ -221,6 +221,7 @@ struct DeliverParams {
     const uint32_t* seg;
     const uint32_t* words;
     const uint32_t* pre;          // pre-decoded rows (partition-word delivery)
+    int32_t max_delay;            // longest delay of any synapse (partition-word delivery)
     const int32_t* wtab;
     int32_t* ring;
     unsigned long long* counters;
