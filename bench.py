@@ -71,8 +71,8 @@ K_STEP_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of on
                          "full size, where fewer rows stay L2-resident between spikes")
 # k_deliver_words, 20,000-spike lists on the small case (scale 0.4): ncu
 # dram__bytes_read + write of three launches over their mean synaptic events
-K_DELIVER_WORDS_DRAM_BYTES_PER_EVENT = ((138.634752 + 138.895360 + 139.256832) +
-                                        (3.372800 + 3.639808 + 3.398656)) * 1e6 / 3.0 / 31.06e6
+K_DELIVER_WORDS_DRAM_BYTES_PER_EVENT = ((135.067904 + 135.324672 + 135.687424) +
+                                        (3.596288 + 3.186432 + 3.619328)) * 1e6 / 3.0 / 31.06e6
 
 
 def load_peaks():
