@@ -380,10 +380,9 @@ def extra_grad(pkg, workload, torch, stream, reps=3):
             "note": "the adjoint grows ~e^0.039 per step through the chaotic dynamics: over "
                     "200 ms max|g| reaches ~4e31, so the gradient's value is dominated by that "
                     "growth; the figure times the computation, not its usefulness for training",
-            # per gradient: one k_step per checkpoint segment (forward, with the
-            # trajectory recorded), one k_adjoint_part per segment, the fold and
-            # the reduction
-            "gpu_launches": 2 * ((n_steps + every - 1) // every) + 2,
+            # per gradient: one k_step (the forward, trajectory recorded), one
+            # k_adjoint_part, the fold and the reduction
+            "gpu_launches": 4,
             "clocks": clk.summary(),
             "config": {"workload": "10%% microcircuit (7,717 neurons), %d time steps, checkpoints "
                                    "every %d steps, gradient w.r.t. 64 projection scales and nu"
@@ -923,10 +922,9 @@ def run_grad(args):
                    "l2": "not flushed; wall-clock per gradient including host marshalling"},
         "loss": loss, "grad_abs_max": float(gs.abs().max()), "grad_nu": float(gn),
         "clocks": clk.summary(),
-        # per gradient: one k_step per checkpoint segment (forward, with the
-        # trajectory recorded), one k_adjoint_part per segment, the fold and
-        # the reduction
-        "gpu_launches": args.steps * (2 * ((n_steps + every - 1) // every) + 2),
+        # per gradient: one k_step (the forward, trajectory recorded), one
+        # k_adjoint_part, the fold and the reduction
+        "gpu_launches": args.steps * 4,
     }
     print(json.dumps(line), flush=True)
 

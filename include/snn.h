@@ -375,8 +375,10 @@ int snn_set_params(snn_net* net, const double* scales, double nu_bg);
 
 /*
  * snn_grad_forward -- run n_steps from the current state as snn_step does,
- * keeping a device checkpoint of the full state every ckpt_every steps, and
- * return the population rates (Hz) over those steps in rates_host[8].
+ * recording the trajectory when it fits the trace budget (see
+ * snn_grad_set_trace_budget), else keeping a device checkpoint of the full
+ * state every ckpt_every steps, and return the population rates (Hz) over
+ * those steps in rates_host[8].
  * snn_grad_backward -- given g_rate[8] = dL/d rate_p of any loss of those
  * rates, return dL/d alpha (g_alpha[p*8 + q]) and dL/d nu_bg (*g_nu) by
  * backpropagation through time: each segment's trajectory (recorded by the

@@ -454,24 +454,27 @@ int snn_grad_forward(snn_net* net, int64_t n_steps, int32_t ckpt_every, double* 
     if (!net->grad) net->grad = new snn_grad();
     snn_grad* g = net->grad;
     const int n = net->n;
-    const int32_t seg = (int32_t)std::min<int64_t>(ckpt_every, n_steps);
-    const int32_t n_seg = (int32_t)((n_steps + seg - 1) / seg);
-    g->ready = false;
-    g->ring_words = ring_words(net);
-    g->ckpt_bytes = (state_bytes(net) + 255) / 256 * 256;
-    if (g->ckpt && g->ckpt_cap < (size_t)n_seg + 1) {
-        cudaFree(g->ckpt);
-        g->ckpt = nullptr;
-    }
-    if (!g->ckpt) {
-        GCALL(galloc(&g->ckpt, g->ckpt_bytes * ((size_t)n_seg + 1), "gradient checkpoints"));
-        g->ckpt_cap = (size_t)n_seg + 1;
-    }
-    // the trace of every step when it fits, else of one segment
+    // the trace of every step when it fits (one launch each way, no
+    // checkpoints), else of one checkpoint segment at a time
     size_t free_b = 0, total_b = 0;
     GCK(cudaMemGetInfo(&free_b, &total_b));
     const size_t full_bytes = (size_t)n_steps * n * (sizeof(float) + 1);
     const bool full = (int64_t)full_bytes <= g->trace_budget && full_bytes <= free_b / 4;
+    const int32_t seg = full ? (int32_t)n_steps : (int32_t)std::min<int64_t>(ckpt_every, n_steps);
+    const int32_t n_seg = (int32_t)((n_steps + seg - 1) / seg);
+    g->ready = false;
+    g->ring_words = ring_words(net);
+    g->ckpt_bytes = (state_bytes(net) + 255) / 256 * 256;
+    if (!full) {
+        if (g->ckpt && g->ckpt_cap < (size_t)n_seg + 1) {
+            cudaFree(g->ckpt);
+            g->ckpt = nullptr;
+        }
+        if (!g->ckpt) {
+            GCALL(galloc(&g->ckpt, g->ckpt_bytes * ((size_t)n_seg + 1), "gradient checkpoints"));
+            g->ckpt_cap = (size_t)n_seg + 1;
+        }
+    }
     const int32_t tr_steps = full ? (int32_t)n_steps : seg;
     if (g->tr_u && g->tr_cap < tr_steps) {
         cudaFree(g->tr_u);
@@ -496,11 +499,11 @@ int snn_grad_forward(snn_net* net, int64_t n_steps, int32_t ckpt_every, double* 
         sp.tr_len = (int32_t)n_steps;
     }
     for (int32_t c = 0; c < n_seg; ++c) {
-        GCK(save_ckpt(net, g->ckpt + (size_t)c * g->ckpt_bytes));
+        if (!full) GCK(save_ckpt(net, g->ckpt + (size_t)c * g->ckpt_bytes));
         const int64_t len = std::min<int64_t>(seg, n_steps - (int64_t)c * seg);
         GCK(net_launch(net, sp, t0 + (int64_t)c * seg, len));
     }
-    GCK(save_ckpt(net, g->ckpt + (size_t)n_seg * g->ckpt_bytes));
+    if (!full) GCK(save_ckpt(net, g->ckpt + (size_t)n_seg * g->ckpt_bytes));
     unsigned long long cnt[kMaxPop];
     GCK(cudaMemcpyAsync(cnt, net->d_pop_spikes, sizeof(cnt), cudaMemcpyDeviceToHost, s));
     GCK(cudaStreamSynchronize(s));
@@ -744,8 +747,9 @@ int snn_grad_backward(snn_net* net, const double* g_rate, double* g_alpha, doubl
     k_grad_reduce<<<kMaxPop * kMaxPop + 1, 512, 0, s>>>(n, net->n_pop, g->pop_start, g->gA, g->gN, g->out + kMaxPop * kMaxPop + 1,
                                      g->out);
     GCK(cudaGetLastError());
-    // back to the state after the forward, with the caller's counters
-    GCK(load_ckpt(net, g->ckpt + (size_t)g->n_seg * g->ckpt_bytes));
+    // back to the state after the forward (only the recomputation changed
+    // it), with the caller's counters
+    if (!g->full_trace) GCK(load_ckpt(net, g->ckpt + (size_t)g->n_seg * g->ckpt_bytes));
     GCK(cudaMemcpyAsync(net->d_counters, g->saved, 16, cudaMemcpyDeviceToDevice, s));
     GCK(cudaMemcpyAsync(net->d_pop_spikes, g->saved + 2, 8 * kMaxPop, cudaMemcpyDeviceToDevice, s));
     GCK(cudaMemcpyAsync(net->d_ras_n, g->saved_ras, 4 * P, cudaMemcpyDeviceToDevice, s));
