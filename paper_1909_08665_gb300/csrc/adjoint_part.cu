@@ -8,7 +8,7 @@
 // sources of each partition into G groups: CTA (c, g) keeps, for the whole
 // launch, the lI window of partition c (slots t + 1 .. t + R - 1 of its
 // neurons) and the runs of its source group into c (the pre-decoded entries,
-// re-packed as weight index, delay and local target) in shared memory.  Its
+// re-packed as weight index and window cell offset) in shared memory.  Its
 // share of the gather then reads shared memory only.  Each source's partial
 // sum over its run into c goes to a global array; after the step's grid
 // barrier every CTA of partition c adds the partials of its partition's
@@ -39,8 +39,8 @@ namespace {
 constexpr int kApThreads = 512;
 constexpr int kApWarps = kApThreads / 32;
 constexpr uint32_t kApNone = 0xffffffffu;
-constexpr uint32_t kApLocBits = 13;          // local target < 2^13
-constexpr uint32_t kApWBits = 19;            // weight index << 19 | delay << 13 | local
+constexpr uint32_t kApWBits = 19;            // weight index << 19 | window cell offset
+constexpr uint32_t kApOffMask = (1u << kApWBits) - 1u;
 constexpr uint32_t kApChunk = 32;           // entries per lane before a run is split
 constexpr uint32_t kApMaxChunks = 4;         // lanes one source's run is split over
 constexpr int kApPre = 4;                    // neurons per thread in the membrane phase (ncmax <= 2048)
@@ -56,12 +56,15 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c = (int)blockIdx.x / p.groups, g = (int)blockIdx.x % p.groups;
     const uint32_t ncmax = (uint32_t)p.ncmax, R = (uint32_t)p.ring_r;
+    // window rows padded to whole 32-word bank rounds: a cell's bank is
+    // its target's, whatever the slot (the plan orders entries by it)
+    const uint32_t ws = (ncmax + 31u) & ~31u;
     const size_t n = (size_t)p.n;
-    // shared memory: the image [img_max], the window [R][ncmax], the weights
+    // shared memory: the image [img_max], the window [R][ws], the weights
     // of the partition's target populations (forward, pA; base) and the
     // adjoint state of its neurons
     float* win = reinterpret_cast<float*>(s_img + p.img_max);
-    float* wf = win + (size_t)R * ncmax;
+    float* wf = win + (size_t)R * ws;
     float* wb = wf + (size_t)p.span_max * kMaxPop * kWCodes + 4;
     // one zero past each table: the weight of the padding entries
     const uint32_t w_zero = (uint32_t)p.span_max * kMaxPop * kWCodes;
@@ -105,14 +108,16 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
     for (uint32_t k = tid; k < (R - 1) * nc; k += kApThreads) {
         const uint32_t d = 1 + k / nc, i = k - (d - 1) * nc;
         const int64_t tt = t_top + d;
-        win[(uint32_t)(tt % R) * ncmax + i] = __ldcg(&p.lring[(size_t)(tt & (kRing - 1)) * n + lo + i]);
+        win[(uint32_t)(tt % R) * ws + i] = __ldcg(&p.lring[(size_t)(tt & (kRing - 1)) * n + lo + i]);
     }
     __syncthreads();
 
     uint32_t tD = (uint32_t)(t_top % R);      // window slot of step t
+    const uint32_t RW = R * ws;               // window words
     uint32_t gen = 0;
     for (int s = p.len - 1; s >= 0; --s) {
         const int64_t t = p.t_first + s;
+        const uint32_t base_t = tD * ws;
         const uint8_t* fl = p.tr_f + (size_t)s * n;
         float* pds = p.pds + (size_t)(s & 1) * p.n_part * n;
         // ---- partial spike adjoints: the runs of this CTA's sources into c ----
@@ -136,13 +141,15 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
 #pragma unroll
             for (int k = 0; k < kMaxPop; ++k) pa[k] = 0.f;
             const uint32_t* ep = ent + eb + lane;
+            // entry: weight index << 19 | delay * ws + target; the window
+            // cell of step t + delay is that offset plus t's row, wrapped
 #pragma unroll 4
             for (uint32_t k = 0; k < lm; ++k) {
                 const uint32_t e = ep[k * 32];
                 const uint32_t wi = e >> kApWBits;
-                uint32_t sl = tD + ((e >> kApLocBits) & 63u);
-                sl -= sl >= R ? R : 0u;
-                const float lv = win[sl * ncmax + (e & ((1u << kApLocBits) - 1u))];
+                uint32_t a = base_t + (e & kApOffMask);
+                a -= a >= RW ? RW : 0u;
+                const float lv = win[a];
                 acc = __fadd_rn(acc, __fmul_rn(wf[wi], lv));
                 if (spk) {
                     const float v = __fmul_rn(wb[wi], lv);
@@ -206,7 +213,7 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
             s_lu[i] = __fadd_rn(__fmul_rn(ds, slope), __fmul_rn(__fsub_rn(1.f, sv), lub));
             s_lI[i] = lIt;
             s_mn[i] = (uint8_t)((f >> 1) & 1u);
-            win[tD * ncmax + i] = lIt;
+            win[tD * ws + i] = lIt;
             if (g == 0) {
                 p.gN[gi] += (double)lIt;
                 __stcg(&p.lring[(size_t)((uint32_t)t & (kRing - 1)) * n + gi], lIt);
@@ -276,7 +283,10 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
             span_max = std::max(span_max, pop_of(part_lo[c + 1] - 1) - pop_of(part_lo[c]) + 1);
     const uint32_t w_zero = (uint32_t)span_max * kMaxPop * kWCodes;
     if (w_zero >= (1u << (32 - kApWBits))) return 1;
-    const uint32_t e_pad = (w_zero << kApWBits) | (1u << kApLocBits);
+    // window rows padded to whole bank rounds (as the kernel does)
+    const uint32_t wsp = ((uint32_t)ncmax + 31u) & ~31u;
+    if ((size_t)kRing * wsp > kApOffMask) return 1;
+    const uint32_t e_pad = (w_zero << kApWBits) | wsp;       // delay 1, target 0, weight 0
     std::vector<uint32_t> img;
     std::vector<uint32_t> off(1, 0u);
     int R = 2;
@@ -339,23 +349,64 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
                 for (uint32_t l = 0; l < 32; ++l) lm = std::max(lm, lanes[L * 32 + l].len);
                 head[kApHeader + L] = lm;
                 head[kApHeader + n_lg + L] = (uint32_t)ents.size();
-                for (uint32_t k = 0; k < lm; ++k)
-                    for (uint32_t l = 0; l < 32; ++l) {
-                        const Lane& ln = lanes[L * 32 + l];
-                        uint32_t e = e_pad;
-                        if (ln.j >= 0 && k < ln.len) {
-                            const uint32_t pe = pre[seg[(size_t)ln.j * (n_part + 1) + c] + ln.k0 + k];
-                            const uint32_t off_e = pe & kPreOffMask;
-                            const uint32_t d = off_e / (uint32_t)ncmax, loc = off_e % (uint32_t)ncmax;
-                            const uint32_t wi = (pe >> kPreOffBits) - (uint32_t)p_lo * kMaxPop * kWCodes;
-                            if (d < 1 || d >= (uint32_t)kRing || (int32_t)loc >= nc ||
-                                wi >= (uint32_t)span * kMaxPop * kWCodes)
-                                return -2;
-                            R = std::max(R, (int)d + 1);
-                            e = (wi << kApWBits) | (d << kApLocBits) | loc;
-                        }
-                        ents.push_back(e);
+                // each lane's entries, re-packed
+                std::vector<uint32_t> le[32];
+                for (uint32_t l = 0; l < 32; ++l) {
+                    const Lane& ln = lanes[L * 32 + l];
+                    for (uint32_t k = 0; ln.j >= 0 && k < ln.len; ++k) {
+                        const uint32_t pe = pre[seg[(size_t)ln.j * (n_part + 1) + c] + ln.k0 + k];
+                        const uint32_t off_e = pe & kPreOffMask;
+                        const uint32_t d = off_e / (uint32_t)ncmax, loc = off_e % (uint32_t)ncmax;
+                        const uint32_t wi = (pe >> kPreOffBits) - (uint32_t)p_lo * kMaxPop * kWCodes;
+                        if (d < 1 || d >= (uint32_t)kRing || (int32_t)loc >= nc ||
+                            wi >= (uint32_t)span * kMaxPop * kWCodes)
+                            return -2;
+                        R = std::max(R, (int)d + 1);
+                        le[l].push_back((wi << kApWBits) | (d * wsp + loc));
                     }
+                }
+                // The order of a lane's entries is free (its sum has a fixed
+                // order either way): column k takes from each lane an entry
+                // whose weight bank (weight index mod 32) and window bank
+                // (target mod 32) no lane of the column used yet, if it has
+                // one; a lane with spare columns may wait (a zero-weight
+                // entry) rather than collide.  Lanes with the most entries
+                // left choose first.
+                for (uint32_t k = 0; k < lm; ++k) {
+                    uint32_t used_w = 0u, used_l = 0u;
+                    uint32_t col[32];
+                    int ord[32];
+                    for (int l = 0; l < 32; ++l) {
+                        col[l] = e_pad;
+                        ord[l] = l;
+                    }
+                    std::stable_sort(ord, ord + 32, [&](int a, int b) { return le[a].size() > le[b].size(); });
+                    for (int oi = 0; oi < 32; ++oi) {
+                        const int l = ord[oi];
+                        if (le[l].empty()) continue;
+                        size_t best = 0;
+                        int best_cost = 3;
+                        for (size_t q = 0; q < le[l].size(); ++q) {
+                            const uint32_t e = le[l][q];
+                            const int cost = (int)((used_w >> ((e >> kApWBits) & 31u)) & 1u) +
+                                             (int)((used_l >> (e & 31u)) & 1u);
+                            if (cost < best_cost) {
+                                best_cost = cost;
+                                best = q;
+                                if (cost == 0) break;
+                            }
+                        }
+                        const bool slack = le[l].size() < (size_t)(lm - k);
+                        if (best_cost > 0 && slack) continue;
+                        const uint32_t e = le[l][best];
+                        le[l][best] = le[l].back();
+                        le[l].pop_back();
+                        used_w |= 1u << ((e >> kApWBits) & 31u);
+                        used_l |= 1u << (e & 31u);
+                        col[l] = e;
+                    }
+                    for (int l = 0; l < 32; ++l) ents.push_back(col[l]);
+                }
             }
             for (uint32_t l = 0; l < 32 * n_lg; ++l) {
                 head[kApHeader + 2 * n_lg + l] = lanes[l].j >= 0 ? (uint32_t)lanes[l].j : kApNone;
@@ -384,7 +435,8 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
             img_max = std::max(img_max, head.size());
         }
     }
-    const size_t smem = img_max * 4 + (size_t)R * ncmax * 4 + (size_t)2 * (span_max * kMaxPop * kWCodes + 4) * 4 +
+    const size_t ws = ((size_t)ncmax + 31) / 32 * 32;
+    const size_t smem = img_max * 4 + (size_t)R * ws * 4 + (size_t)2 * (span_max * kMaxPop * kWCodes + 4) * 4 +
                         (size_t)ncmax * 8 + (size_t)ncmax;
     if (smem > (size_t)optin) return 1;
     plan->grid = n_part * G;
