@@ -182,49 +182,80 @@ struct FlatSmem {
     uint32_t* pre;               // [kFlatChunk + 1] exclusive prefix of row lengths
     uint32_t* meta;              // [kFlatChunk] instance << 3 | source population
     uint32_t* wsum;              // [kBWarps] scan partials
+    // the first chunk of a step's flat list, fetched ahead by asynchronous
+    // copies (k_batch): spike ids, their row bounds, the list length
+    unsigned long long* pf_rs;   // [kFlatChunk][2] row_start[j], row_start[j + 1]
+    const unsigned long long** rsp;   // [n_inst] row starts of each instance
+    uint32_t* pf_ids;            // [kFlatChunk]
+    uint32_t* pf_nf;             // [4]
 };
 
 __host__ __device__ inline size_t flat_smem_bytes(int n_inst) {
-    return (size_t)kFlatChunk * sizeof(void*) + (size_t)n_inst * 8 * sizeof(int32_t) +
-           ((size_t)kFlatChunk + 1) * 4 + (size_t)kFlatChunk * 4 + kBWarps * 4;
+    return (size_t)kFlatChunk * sizeof(void*) + (size_t)kFlatChunk * 16 + (size_t)n_inst * sizeof(void*) +
+           (size_t)n_inst * 8 * sizeof(int32_t) + ((size_t)kFlatChunk + 1) * 4 + (size_t)kFlatChunk * 4 +
+           kBWarps * 4 + (size_t)kFlatChunk * 4 + 16;
 }
 
 __device__ inline FlatSmem flat_smem(unsigned char* base, int n_inst) {
     FlatSmem F;
     F.beg = reinterpret_cast<const uint32_t**>(base);
-    F.ps = reinterpret_cast<int32_t*>(base + (size_t)kFlatChunk * sizeof(void*));
+    F.pf_rs = reinterpret_cast<unsigned long long*>(base + (size_t)kFlatChunk * sizeof(void*));
+    F.rsp = reinterpret_cast<const unsigned long long**>(F.pf_rs + 2 * (size_t)kFlatChunk);
+    F.ps = reinterpret_cast<int32_t*>(F.rsp + n_inst);
     F.pre = reinterpret_cast<uint32_t*>(F.ps + (size_t)n_inst * 8);
     F.meta = F.pre + kFlatChunk + 1;
     F.wsum = F.meta + kFlatChunk;
+    F.pf_ids = F.wsum + kBWarps;
+    F.pf_nf = F.pf_ids + kFlatChunk;
     return F;
 }
 
 __device__ inline void flat_load_ps(const BatchParams& p, const FlatSmem& F) {
     for (int k = threadIdx.x; k < p.n_inst * 8; k += kBThreads) F.ps[k] = __ldg(&p.ps_all[k]);
+    for (int k = threadIdx.x; k < p.n_inst; k += kBThreads) F.rsp[k] = p.cold[k].row_start;
+}
+
+// asynchronous global -> shared copies (completed by cp_async_wait)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 // Flat tiling: the rows of the nf spikes in `list`, spread over every warp of
 // the grid.  Every CTA stages the same rows; CTA 0 alone counts the events.
+// prefetched: the first chunk's ids and row bounds are in F.pf_ids / F.pf_rs
 __device__ void deliver_flat(const BatchParams& p, const int32_t* s_goff, const FlatSmem& F,
-                             const uint32_t* list, uint32_t nf, uint32_t tD, bool count) {
+                             const uint32_t* list, uint32_t nf, uint32_t tD, bool count,
+                             bool prefetched = false) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t ntot = (size_t)p.ntot;
     for (uint32_t f0 = 0; f0 < nf; f0 += kFlatChunk) {
         const uint32_t mc = min((uint32_t)kFlatChunk, nf - f0);
+        const bool pf = prefetched && f0 == 0;
         // stage two rows per thread: start, length, instance and population
         uint32_t len[2] = {0u, 0u};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint32_t k = (uint32_t)tid * 2u + (uint32_t)h;
             if (k < mc) {
-                const int32_t gi = (int32_t)__ldcg(&list[f0 + k]);
+                const int32_t gi = pf ? (int32_t)F.pf_ids[k] : (int32_t)__ldcg(&list[f0 + k]);
                 const int ki = inst_of(s_goff, p.n_inst, gi);
                 const int32_t j = gi - s_goff[ki];
                 int q = 0;
 #pragma unroll
                 for (int m = 1; m < kMaxPop; ++m) q += j >= F.ps[ki * 8 + m] ? 1 : 0;
                 const InstCold& I = p.cold[ki];
-                const unsigned long long b = I.row_start[j], e = I.row_start[j + 1];
+                const unsigned long long b = pf ? F.pf_rs[2 * k] : I.row_start[j];
+                const unsigned long long e = pf ? F.pf_rs[2 * k + 1] : I.row_start[j + 1];
                 F.beg[k] = I.words + b;
                 F.meta[k] = ((uint32_t)ki << 3) | (uint32_t)q;
                 len[h] = (uint32_t)(e - b);
@@ -413,6 +444,15 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ 
         if (!grid_sync(p, gen, &s_abort)) break;
         // counters of step t + 2: last read in D(t - 2), next written in A(t + 2)
         if (blockIdx.x == 0 && tid < kTilings) p.cnt[(uint32_t)((t + 2) & 3) * kTilings + tid] = 0u;
+        // D(t)'s flat list, fetched while C(t) and A(t + 1) run: its length
+        // and the first kFlatChunk ids now (past the length: unused), the
+        // rows' bounds after C(t)
+        const uint32_t* lf_t = p.list + ((size_t)(t & 1) * kTilings + 2) * ntot;
+        {
+            const uint32_t lim = (uint32_t)min((size_t)kFlatChunk, ntot);
+            if (tid == 0) cp_async4(F.pf_nf, &p.cnt[(uint32_t)(t & 3) * kTilings + 2]);
+            for (uint32_t k = tid; k < lim; k += kBThreads) cp_async4(&F.pf_ids[k], &lf_t[k]);
+        }
 
         // ---- C(t): ring slot t, background, synaptic current ----
         {
@@ -458,8 +498,20 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ 
                                     __fmul_rn(__int2float_rn(acc[k]), 0.00390625f));
             }
         }
+        cp_async_wait();
+        __syncthreads();
+        const uint32_t nf_pf = min(*F.pf_nf, (uint32_t)kFlatChunk);
+        for (uint32_t k = tid; k < nf_pf; k += kBThreads) {
+            const int32_t gi = (int32_t)F.pf_ids[k];
+            const int ki = inst_of(s_goff, p.n_inst, gi);
+            const unsigned long long* rs = F.rsp[ki] + (gi - s_goff[ki]);
+            cp_async8(&F.pf_rs[2 * k], rs);
+            cp_async8(&F.pf_rs[2 * k + 1], rs + 1);
+        }
         // ---- A(t + 1) ----
         if (s + 1 < n) phase_a(t + 1);
+        cp_async_wait();
+        __syncthreads();
         // ---- D(t): spikes of step t ----
         {
             const uint32_t par4 = (uint32_t)(t & 3), par2 = (uint32_t)(t & 1);
@@ -469,7 +521,7 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const __grid_constant__ 
             const uint32_t* lw = p.list + ((size_t)par2 * kTilings + 0) * ntot;
             const uint32_t* lb = p.list + ((size_t)par2 * kTilings + 1) * ntot;
             const uint32_t* lf = p.list + ((size_t)par2 * kTilings + 2) * ntot;
-            if (nf) deliver_flat(p, s_goff, F, lf, nf, tD, true);
+            if (nf) deliver_flat(p, s_goff, F, lf, nf, tD, true, true);
             // warp w of CTA b takes spikes w * grid + b, spreading them over SMs
             for (uint32_t k = (uint32_t)(tid >> 5) * gridDim.x + blockIdx.x; k < nw;
                  k += (uint32_t)kBWarps * gridDim.x)
