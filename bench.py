@@ -347,7 +347,11 @@ def extra_batch(pkg, workload, torch, stream, hbm_peak, peak_kind, n_inst=64):
 def extra_grad(pkg, workload, torch, stream, reps=3):
     """One surrogate-gradient evaluation of the 10 % microcircuit over 200 ms
     (2000 steps, checkpoints every 100): forward, backward, through the
-    torch.autograd.Function; wall time per evaluation (device-synchronised)."""
+    torch.autograd.Function; wall time per evaluation (device-synchronised).
+    The value is taken with checkpoints every 100 steps, the backward
+    re-running each segment (trace budget 0); the same gradient, bit for bit,
+    with the forward recording the whole trajectory instead is timed beside
+    it."""
     from paper_1909_08665_gb300.autograd import microcircuit_rates
     cfg = workload.microcircuit(0.1)
     targets = torch.as_tensor(workload.target_rates())
@@ -363,26 +367,32 @@ def extra_grad(pkg, workload, torch, stream, reps=3):
         loss.backward()
         return float(loss.item()), float(scales.grad.abs().max())
 
-    one()
-    torch.cuda.synchronize()
-    times = []
-    with ClockSampler(torch.cuda.current_device()) as clk:
+    def timed(budget):
+        net.set_grad_trace_budget(budget)
+        one()
+        torch.cuda.synchronize()
+        times = []
         for _ in range(reps):
             t0 = time.perf_counter()
-            loss, gmax = one()
+            res = one()
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
+        return 1e3 * float(np.median(times)), res
+
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms, (loss, gmax) = timed(0)
+        ms_rec, _ = timed(4 << 30)
     net.close()
-    ms = 1e3 * float(np.median(times))
     return {"metric": "surrogate-gradient evaluations/s (10% microcircuit, 200 ms, rate MSE)",
             "value": 1e3 / ms, "unit": "gradients/s", "ms_per_gradient": ms, "reps": reps,
             "loss": loss, "grad_abs_max": gmax,
             "note": "the adjoint grows ~e^0.039 per step through the chaotic dynamics: over "
                     "200 ms max|g| reaches ~4e31, so the gradient's value is dominated by that "
                     "growth; the figure times the computation, not its usefulness for training",
-            # per gradient: one k_step (the forward, trajectory recorded), one
-            # k_adjoint_part, the fold and the reduction
-            "gpu_launches": 4,
+            "ms_per_gradient_recorded_trajectory": ms_rec,
+            # per gradient: one k_step per checkpoint segment forward, k_step +
+            # k_adjoint_part per segment backward, the fold and the reduction
+            "gpu_launches": 3 * ((n_steps + every - 1) // every) + 2,
             "clocks": clk.summary(),
             "config": {"workload": "10%% microcircuit (7,717 neurons), %d time steps, checkpoints "
                                    "every %d steps, gradient w.r.t. 64 projection scales and nu"
@@ -890,6 +900,10 @@ def run_grad(args):
     net = pkg.Microcircuit(cfg, stream=stream)
     start = net.save_state()
     n_steps, every = 2000, 100
+    # 0: checkpoints every 100 steps, the backward re-running each segment;
+    # larger: the forward records the whole trajectory when it fits
+    net.set_grad_trace_budget(args.grad_trace_budget)
+    recorded = 5 * n_steps * net.n <= args.grad_trace_budget
 
     def one():
         scales = torch.ones(8, 8, dtype=torch.float64, requires_grad=True)
@@ -916,15 +930,17 @@ def run_grad(args):
         "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "10%% microcircuit (7,717 neurons), %d time steps, checkpoints "
-                               "every %d steps, gradient w.r.t. 64 projection scales and nu"
-                               % (n_steps, every),
+        "config": {"workload": "10%% microcircuit (7,717 neurons), %d time steps, %s, gradient "
+                               "w.r.t. 64 projection scales and nu"
+                               % (n_steps, "trajectory recorded by the forward" if recorded
+                                  else "checkpoints every %d steps" % every),
                    "l2": "not flushed; wall-clock per gradient including host marshalling"},
         "loss": loss, "grad_abs_max": float(gs.abs().max()), "grad_nu": float(gn),
         "clocks": clk.summary(),
-        # per gradient: one k_step (the forward, trajectory recorded), one
-        # k_adjoint_part, the fold and the reduction
-        "gpu_launches": args.steps * 4,
+        # per gradient, recorded: one k_step, one k_adjoint_part, the fold and
+        # the reduction; checkpointed: one k_step per segment forward, k_step +
+        # k_adjoint_part per segment backward, the fold and the reduction
+        "gpu_launches": args.steps * (4 if recorded else 3 * ((n_steps + every - 1) // every) + 2),
     }
     print(json.dumps(line), flush=True)
 
@@ -945,6 +961,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 20,000-spike delivery, 4x, batch and gradient keys")
     ap.add_argument("--instances", type=int, default=64, help="instances of --workload batch")
+    ap.add_argument("--grad-trace-budget", type=int, default=0,
+                    help="--workload grad: trajectory bytes kept by the forward (0: checkpoints)")
     ap.add_argument("--deliver-scale", default="1.0,4.0", help="--workload deliver: scales")
     ap.add_argument("--deliver-spikes", default="25,93,4000,20000", help="--workload deliver: list sizes")
     ap.add_argument("--deliver-tilings", default="0,1,2,3", help="--workload deliver: tilings (4: clusters)")
