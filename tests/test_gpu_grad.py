@@ -254,6 +254,9 @@ def test_gradient_independent_of_checkpoint_spacing(config3):
     for ga, gn in out[1:]:
         np.testing.assert_array_equal(ga, out[0][0])
         assert gn == out[0][1]
+    with pytest.raises(pkg.SnnError) as e:
+        net.set_grad_trace_budget(-1)
+    assert e.value.code == pkg.SNN_ERR_INVALID
 
 
 def test_backward_restores_state_counters_and_raster():
