@@ -3,6 +3,9 @@
 // partition, for networks whose rows fit in the SMs' shared memory.
 //
 // The gather of step t is ds_j = gs + sum over row j of (w / 256) lI_{i,t+d}.
+// Only its delay-1 entries need step t + 1's lI; the rest ("far", delay >= 2)
+// is computed while the grid barrier of step t + 1 completes (a split
+// barrier: arrive, far gather of step t, wait), the near part after it.
 // Gathered from a global lI ring, it costs one L2 request per synapse and
 // step.  Here the targets are split into the network's partitions and the
 // sources of each partition into G groups: CTA (c, g) keeps, for the whole
@@ -45,8 +48,9 @@ constexpr uint32_t kApChunk = 32;           // entries per lane before a run is 
 constexpr uint32_t kApMaxChunks = 4;         // lanes one source's run is split over
 constexpr int kApPre = 4;                    // neurons per thread in the membrane phase (ncmax <= 2048)
 constexpr int kApHeader = 8;                 // n_lg, nc, p_lo, span, e_off, 0, 0, 0
-// header, then lenmax[n_lg], ebase[n_lg], src[32 n_lg], chunks[32 n_lg] (m on
-// a source's first lane, else 0),
+// header, then for the entries of delay >= 2 ("far") lenmax[n_lg] and
+// ebase[n_lg], for those of delay 1 ("near") lenmax[n_lg] and ebase[n_lg],
+// src[32 n_lg], chunks[32 n_lg] (m on a source's first lane, else 0),
 // warp_first[kApWarps + 1], lg_order[n_lg], then the entries at e_off
 
 __global__ void __launch_bounds__(kApThreads, 1)
@@ -70,7 +74,8 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
     const uint32_t w_zero = (uint32_t)p.span_max * kMaxPop * kWCodes;
     float* s_lu = wb + w_zero + 4;
     float* s_lI = s_lu + ncmax;
-    uint8_t* s_mn = reinterpret_cast<uint8_t*>(s_lI + ncmax);
+    float* s_far = s_lI + ncmax;                 // [max_lg][32] far sums of the lanes
+    uint8_t* s_mn = reinterpret_cast<uint8_t*>(s_far + (size_t)p.max_lg * 32);
 
     if (tid == 0) s_abort = 0u;
     {
@@ -81,9 +86,11 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
     }
     __syncthreads();
     const uint32_t n_lg = s_img[0], nc = s_img[1], p_lo = s_img[2], span = s_img[3];
-    const uint32_t* lenmax = s_img + kApHeader;
+    const uint32_t* lenmax = s_img + kApHeader;      // far columns
     const uint32_t* ebase = lenmax + n_lg;
-    const uint32_t* srcs = ebase + n_lg;
+    const uint32_t* lenmax_n = ebase + n_lg;         // near columns
+    const uint32_t* ebase_n = lenmax_n + n_lg;
+    const uint32_t* srcs = ebase_n + n_lg;
     const uint32_t* lens = srcs + 32 * n_lg;
     const uint32_t* warp_first = lens + 32 * n_lg;
     const uint32_t* lg_order = warp_first + kApWarps + 1;
@@ -112,37 +119,28 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
     }
     __syncthreads();
 
-    uint32_t tD = (uint32_t)(t_top % R);      // window slot of step t
     const uint32_t RW = R * ws;               // window words
-    uint32_t gen = 0;
-    for (int s = p.len - 1; s >= 0; --s) {
-        const int64_t t = p.t_first + s;
-        const uint32_t base_t = tD * ws;
-        const uint8_t* fl = p.tr_f + (size_t)s * n;
-        float* pds = p.pds + (size_t)(s & 1) * p.n_part * n;
-        // ---- partial spike adjoints: the runs of this CTA's sources into c ----
-        // this step's trace of the partition's neurons, loaded before the barrier
-        const float* ut = p.tr_u + (size_t)s * n;
-        float u_pre[kApPre];
-        uint8_t f_pre[kApPre];
-#pragma unroll
-        for (int k = 0; k < kApPre; ++k) {
-            const uint32_t i = (uint32_t)tid + (uint32_t)k * kApThreads;
-            u_pre[k] = i < nc ? ut[lo + i] : 0.f;
-            f_pre[k] = i < nc ? fl[lo + i] : (uint8_t)0;
-        }
+    // The gather of step tt, far (delay >= 2: window steps tt + 2 .. , all
+    // final before step tt + 1's membrane phase) or near (delay 1: step tt +
+    // 1).  The far sums wait in s_far; the near walk adds them, combines a
+    // source's chunks and writes its partial.  Spiking sources' weight
+    // partials go to gAc after each walk.
+    auto walk = [&](int64_t tt, uint32_t tDt, bool far) {
+        const uint8_t* flt = p.tr_f + (size_t)(tt - p.t_first) * n;
+        const uint32_t base_t = tDt * ws;
         for (uint32_t wl = warp_first[warp]; wl < warp_first[warp + 1]; ++wl) {
             const uint32_t L = lg_order[wl];
             const uint32_t j = srcs[L * 32 + lane];
-            const uint32_t lm = lenmax[L], eb = ebase[L];
-            const bool spk = j != kApNone && (fl[j] & 1u) != 0u;
+            const uint32_t lm = far ? lenmax[L] : lenmax_n[L];
+            const uint32_t eb = far ? ebase[L] : ebase_n[L];
+            const bool spk = j != kApNone && (flt[j] & 1u) != 0u;
             float acc = 0.f;
             float pa[kMaxPop];
 #pragma unroll
             for (int k = 0; k < kMaxPop; ++k) pa[k] = 0.f;
             const uint32_t* ep = ent + eb + lane;
             // entry: weight index << 19 | delay * ws + target; the window
-            // cell of step t + delay is that offset plus t's row, wrapped
+            // cell of step tt + delay is that offset plus tt's row, wrapped
 #pragma unroll 4
             for (uint32_t k = 0; k < lm; ++k) {
                 const uint32_t e = ep[k * 32];
@@ -161,11 +159,20 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
             // the chunks of a source sit in consecutive lanes; its first lane
             // (m > 0) adds them in chunk order
             const uint32_t m = lens[L * 32 + lane];
-            float tot = acc;
+            if (far) {
+                s_far[L * 32 + lane] = acc;
+            } else {
+                acc = __fadd_rn(s_far[L * 32 + lane], acc);
+                float tot = acc;
 #pragma unroll
-            for (uint32_t r = 1; r < kApMaxChunks; ++r) {
-                const float v = __shfl_down_sync(0xffffffffu, acc, r);
-                if (r < m) tot = __fadd_rn(tot, v);
+                for (uint32_t r = 1; r < kApMaxChunks; ++r) {
+                    const float v = __shfl_down_sync(0xffffffffu, acc, r);
+                    if (r < m) tot = __fadd_rn(tot, v);
+                }
+                if (m > 0u) {
+                    float* pds = p.pds + (size_t)(tt & 1) * p.n_part * n;
+                    __stcg(&pds[(size_t)c * n + j], tot);
+                }
             }
             if (__any_sync(0xffffffffu, spk)) {
 #pragma unroll
@@ -178,10 +185,7 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
                     }
                     pa[kk] = t2;
                 }
-            }
-            if (m > 0u) {
-                __stcg(&pds[(size_t)c * n + j], tot);
-                if (spk) {
+                if (m > 0u && spk) {
                     double* ga = p.gAc + ((size_t)c * n + j) * kMaxPop;
 #pragma unroll
                     for (int kk = 0; kk < kMaxPop; ++kk)
@@ -189,10 +193,61 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
                 }
             }
         }
-        if (!grid_barrier(p.barrier, p.abort_flag, p.status, p.timeout_ns, gen, &s_abort, false))
-            break;
+    };
+    // split grid barrier: every CTA arrives once its partials are written,
+    // does the next step's far gather, then waits
+    uint32_t gen = 0;
+    auto arrive = [&]() {
+        __syncthreads();
+        if (tid == 0) red_release_gpu_add(p.barrier, 1u);
+    };
+    auto wait = [&]() -> bool {
+        if (tid == 0) {
+            const uint32_t target = (gen + 1u) * gridDim.x;
+            const uint64_t t_start = globaltimer_ns();
+            uint32_t iter = 0;
+            while (ld_acquire_gpu(p.barrier) < target) {
+                if ((++iter & 255u) == 0u) {
+                    if (ld_relaxed_gpu(p.abort_flag) != 0u) { s_abort = 1u; break; }
+                    if (globaltimer_ns() - t_start > p.timeout_ns) {
+                        atomicOr(p.status, kStatusTimeout);
+                        atomicExch(p.abort_flag, 1u);
+                        s_abort = 1u;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        ++gen;
+        return s_abort == 0u;
+    };
+
+    uint32_t tD = (uint32_t)(t_top % R);      // window slot of step t
+    // step t_top's gather, both parts, before the first barrier
+    walk(t_top, tD, true);
+    __syncwarp();
+    walk(t_top, tD, false);
+    arrive();
+    for (int s = p.len - 1; s >= 0; --s) {
+        const int64_t t = p.t_first + s;
+        const uint32_t tD1 = tD == 0u ? R - 1u : tD - 1u;     // window slot of step t - 1
+        // this step's trace of the partition's neurons, loaded before the wait
+        const uint8_t* fl = p.tr_f + (size_t)s * n;
+        const float* ut = p.tr_u + (size_t)s * n;
+        float u_pre[kApPre];
+        uint8_t f_pre[kApPre];
+#pragma unroll
+        for (int k = 0; k < kApPre; ++k) {
+            const uint32_t i = (uint32_t)tid + (uint32_t)k * kApThreads;
+            u_pre[k] = i < nc ? ut[lo + i] : 0.f;
+            f_pre[k] = i < nc ? fl[lo + i] : (uint8_t)0;
+        }
+        // the far part of step t - 1's gather while the other CTAs arrive
+        if (s > 0) walk(t - 1, tD1, true);
+        if (!wait()) break;
         // ---- membrane and current adjoints of partition c's neurons ----
-        float* pds_all = p.pds + (size_t)(s & 1) * p.n_part * n;
+        float* pds_all = p.pds + (size_t)(t & 1) * p.n_part * n;
 #pragma unroll
         for (int kp = 0; kp < kApPre; ++kp) {
             const uint32_t i = (uint32_t)tid + (uint32_t)kp * kApThreads;
@@ -220,7 +275,12 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
             }
         }
         __syncthreads();
-        tD = tD == 0u ? R - 1u : tD - 1u;
+        // the near part of step t - 1's gather (it reads step t), its partials
+        if (s > 0) {
+            walk(t - 1, tD1, false);
+            arrive();
+        }
+        tD = tD1;
     }
     if (g == 0 && s_abort == 0u) {
         for (uint32_t i = tid; i < nc; i += kApThreads) {
@@ -286,11 +346,13 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
     // window rows padded to whole bank rounds (as the kernel does)
     const uint32_t wsp = ((uint32_t)ncmax + 31u) & ~31u;
     if ((size_t)kRing * wsp > kApOffMask) return 1;
-    const uint32_t e_pad = (w_zero << kApWBits) | wsp;       // delay 1, target 0, weight 0
+    const uint32_t e_pad = (w_zero << kApWBits) | wsp;            // delay 1, target 0, weight 0
+    const uint32_t e_pad_far = (w_zero << kApWBits) | (2u * wsp);  // delay 2
     std::vector<uint32_t> img;
     std::vector<uint32_t> off(1, 0u);
     int R = 2;
     size_t img_max = 0;
+    uint32_t max_lg = 0;
     for (int c = 0; c < n_part; ++c) {
         const int32_t nc = part_lo[c + 1] - part_lo[c];
         const int p_lo = nc > 0 ? pop_of(part_lo[c]) : 0;
@@ -337,7 +399,7 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
             }
             const uint32_t n_lg = (uint32_t)((lanes.size() + 31) / 32);
             while (lanes.size() < (size_t)n_lg * 32) lanes.push_back(Lane{-1, 0u, 0u, 0u});
-            const size_t o_wf = kApHeader + 2 * (size_t)n_lg + 64 * (size_t)n_lg;
+            const size_t o_wf = kApHeader + 4 * (size_t)n_lg + 64 * (size_t)n_lg;
             std::vector<uint32_t> head(o_wf + kApWarps + 1 + n_lg, 0u);
             head[0] = n_lg;
             head[1] = (uint32_t)nc;
@@ -345,12 +407,8 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
             head[3] = (uint32_t)span;
             std::vector<uint32_t> ents;
             for (uint32_t L = 0; L < n_lg; ++L) {
-                uint32_t lm = 0;
-                for (uint32_t l = 0; l < 32; ++l) lm = std::max(lm, lanes[L * 32 + l].len);
-                head[kApHeader + L] = lm;
-                head[kApHeader + n_lg + L] = (uint32_t)ents.size();
-                // each lane's entries, re-packed
-                std::vector<uint32_t> le[32];
+                // each lane's entries, re-packed, far (delay >= 2) and near (1)
+                std::vector<uint32_t> le[2][32];
                 for (uint32_t l = 0; l < 32; ++l) {
                     const Lane& ln = lanes[L * 32 + l];
                     for (uint32_t k = 0; ln.j >= 0 && k < ln.len; ++k) {
@@ -362,55 +420,64 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
                             wi >= (uint32_t)span * kMaxPop * kWCodes)
                             return -2;
                         R = std::max(R, (int)d + 1);
-                        le[l].push_back((wi << kApWBits) | (d * wsp + loc));
+                        le[d == 1u ? 1 : 0][l].push_back((wi << kApWBits) | (d * wsp + loc));
                     }
                 }
-                // The order of a lane's entries is free (its sum has a fixed
-                // order either way): column k takes from each lane an entry
-                // whose weight bank (weight index mod 32) and window bank
-                // (target mod 32) no lane of the column used yet, if it has
-                // one; a lane with spare columns may wait (a zero-weight
-                // entry) rather than collide.  Lanes with the most entries
-                // left choose first.
-                for (uint32_t k = 0; k < lm; ++k) {
-                    uint32_t used_w = 0u, used_l = 0u;
-                    uint32_t col[32];
-                    int ord[32];
-                    for (int l = 0; l < 32; ++l) {
-                        col[l] = e_pad;
-                        ord[l] = l;
-                    }
-                    std::stable_sort(ord, ord + 32, [&](int a, int b) { return le[a].size() > le[b].size(); });
-                    for (int oi = 0; oi < 32; ++oi) {
-                        const int l = ord[oi];
-                        if (le[l].empty()) continue;
-                        size_t best = 0;
-                        int best_cost = 3;
-                        for (size_t q = 0; q < le[l].size(); ++q) {
-                            const uint32_t e = le[l][q];
-                            const int cost = (int)((used_w >> ((e >> kApWBits) & 31u)) & 1u) +
-                                             (int)((used_l >> (e & 31u)) & 1u);
-                            if (cost < best_cost) {
-                                best_cost = cost;
-                                best = q;
-                                if (cost == 0) break;
-                            }
+                for (int part = 0; part < 2; ++part) {
+                    uint32_t lm = 0;
+                    for (uint32_t l = 0; l < 32; ++l) lm = std::max(lm, (uint32_t)le[part][l].size());
+                    head[kApHeader + 2 * part * n_lg + L] = lm;
+                    head[kApHeader + (2 * part + 1) * n_lg + L] = (uint32_t)ents.size();
+                    // padding: weight zero, a valid window cell of the part's delays
+                    const uint32_t pad = part == 0 ? e_pad_far : e_pad;
+                    // The order of a lane's entries is free (its sum has a
+                    // fixed order either way): column k takes from each lane
+                    // an entry whose weight bank (weight index mod 32) and
+                    // window bank (target mod 32) no lane of the column used
+                    // yet, if it has one; a lane with spare columns may wait
+                    // (a zero-weight entry) rather than collide.  Lanes with
+                    // the most entries left choose first.
+                    std::vector<uint32_t>* lp = le[part];
+                    for (uint32_t k = 0; k < lm; ++k) {
+                        uint32_t used_w = 0u, used_l = 0u;
+                        uint32_t col[32];
+                        int ord[32];
+                        for (int l = 0; l < 32; ++l) {
+                            col[l] = pad;
+                            ord[l] = l;
                         }
-                        const bool slack = le[l].size() < (size_t)(lm - k);
-                        if (best_cost > 0 && slack) continue;
-                        const uint32_t e = le[l][best];
-                        le[l][best] = le[l].back();
-                        le[l].pop_back();
-                        used_w |= 1u << ((e >> kApWBits) & 31u);
-                        used_l |= 1u << (e & 31u);
-                        col[l] = e;
+                        std::stable_sort(ord, ord + 32, [&](int x, int y) { return lp[x].size() > lp[y].size(); });
+                        for (int oi = 0; oi < 32; ++oi) {
+                            const int l = ord[oi];
+                            if (lp[l].empty()) continue;
+                            size_t best = 0;
+                            int best_cost = 3;
+                            for (size_t q = 0; q < lp[l].size(); ++q) {
+                                const uint32_t e = lp[l][q];
+                                const int cost = (int)((used_w >> ((e >> kApWBits) & 31u)) & 1u) +
+                                                 (int)((used_l >> (e & 31u)) & 1u);
+                                if (cost < best_cost) {
+                                    best_cost = cost;
+                                    best = q;
+                                    if (cost == 0) break;
+                                }
+                            }
+                            const bool slack = lp[l].size() < (size_t)(lm - k);
+                            if (best_cost > 0 && slack) continue;
+                            const uint32_t e = lp[l][best];
+                            lp[l][best] = lp[l].back();
+                            lp[l].pop_back();
+                            used_w |= 1u << ((e >> kApWBits) & 31u);
+                            used_l |= 1u << (e & 31u);
+                            col[l] = e;
+                        }
+                        for (int l = 0; l < 32; ++l) ents.push_back(col[l]);
                     }
-                    for (int l = 0; l < 32; ++l) ents.push_back(col[l]);
                 }
             }
             for (uint32_t l = 0; l < 32 * n_lg; ++l) {
-                head[kApHeader + 2 * n_lg + l] = lanes[l].j >= 0 ? (uint32_t)lanes[l].j : kApNone;
-                head[kApHeader + 2 * n_lg + 32 * n_lg + l] = lanes[l].m;
+                head[kApHeader + 4 * n_lg + l] = lanes[l].j >= 0 ? (uint32_t)lanes[l].j : kApNone;
+                head[kApHeader + 4 * n_lg + 32 * n_lg + l] = lanes[l].m;
             }
             // lane groups to warps, longest first, each to the least loaded warp
             std::vector<std::vector<uint32_t>> per_warp(kApWarps);
@@ -418,7 +485,7 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
             for (uint32_t L = 0; L < n_lg; ++L) {
                 const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
                 per_warp[w].push_back(L);
-                load[w] += head[kApHeader + L] + 1ull;
+                load[w] += head[kApHeader + L] + head[kApHeader + 2 * n_lg + L] + 1ull;
             }
             uint32_t pos = 0;
             for (int w = 0; w < kApWarps; ++w) {
@@ -433,17 +500,19 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
             img.insert(img.end(), head.begin(), head.end());
             off.push_back((uint32_t)img.size());
             img_max = std::max(img_max, head.size());
+            max_lg = std::max(max_lg, n_lg);
         }
     }
     const size_t ws = ((size_t)ncmax + 31) / 32 * 32;
     const size_t smem = img_max * 4 + (size_t)R * ws * 4 + (size_t)2 * (span_max * kMaxPop * kWCodes + 4) * 4 +
-                        (size_t)ncmax * 8 + (size_t)ncmax;
+                        (size_t)ncmax * 8 + (size_t)max_lg * 32 * 4 + (size_t)ncmax;
     if (smem > (size_t)optin) return 1;
     plan->grid = n_part * G;
     plan->groups = G;
     plan->ring_r = R;
     plan->span_max = span_max;
     plan->img_max = (int32_t)img_max;
+    plan->max_lg = (int32_t)max_lg;
     plan->smem = smem;
     cudaError_t e = cudaMalloc(&plan->d_img, sizeof(uint32_t) * std::max<size_t>(img.size(), 4));
     if (e == cudaSuccess) e = cudaMalloc(&plan->d_img_off, sizeof(uint32_t) * off.size());
@@ -474,6 +543,7 @@ cudaError_t launch_adjoint_part(const AdjPartPlan& plan, AdjPartParams& ap, cuda
     ap.ring_r = plan.ring_r;
     ap.span_max = plan.span_max;
     ap.img_max = plan.img_max;
+    ap.max_lg = plan.max_lg;
     ap.img = plan.d_img;
     ap.img_off = plan.d_img_off;
     cudaLaunchConfig_t cfg = {};

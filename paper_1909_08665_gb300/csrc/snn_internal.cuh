@@ -297,7 +297,7 @@ cudaError_t deliver_cluster_check(int ncmax, int n_part, int* max_active_cluster
 // the gather.
 struct AdjPartParams {
     int32_t n, n_pop, n_part, ncmax, len;
-    int32_t groups, ring_r, span_max, img_max;   // set by launch_adjoint_part
+    int32_t groups, ring_r, span_max, img_max, max_lg;   // set by launch_adjoint_part
     int64_t t_first;                 // global step of trace row 0
     float P22, P21, P11, theta;
     float gs[kMaxPop];               // dL/ds per spike of each population
@@ -324,6 +324,7 @@ struct AdjPartParams {
 struct AdjPartPlan {
     int grid = 0, groups = 0, ring_r = 0, span_max = 0;
     int32_t img_max = 0;             // words of the largest CTA image
+    int32_t max_lg = 0;              // most lane groups of one CTA
     size_t smem = 0;
     uint32_t* d_img = nullptr;
     uint32_t* d_img_off = nullptr;   // [grid + 1]
