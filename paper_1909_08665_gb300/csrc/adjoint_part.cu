@@ -75,7 +75,11 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
     float* s_lu = wb + w_zero + 4;
     float* s_lI = s_lu + ncmax;
     float* s_far = s_lI + ncmax;                 // [max_lg][32] far sums of the lanes
-    uint8_t* s_mn = reinterpret_cast<uint8_t*>(s_far + (size_t)p.max_lg * 32);
+    // group 0: the nu sums of the partition's neurons, accumulated here in
+    // the order the global ones would be, read in at the start, written at the end
+    double* s_gN = reinterpret_cast<double*>(
+        (reinterpret_cast<uintptr_t>(s_far + (size_t)p.max_lg * 32) + 7) & ~uintptr_t(7));
+    uint8_t* s_mn = reinterpret_cast<uint8_t*>(s_gN + ncmax);
 
     if (tid == 0) s_abort = 0u;
     {
@@ -109,6 +113,7 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
         s_lu[i] = p.lu[lo + i];
         s_lI[i] = p.lI[lo + i];
         s_mn[i] = p.mnext[lo + i];
+        if (g == 0) s_gN[i] = p.gN[lo + i];
     }
     // the window of the first step processed, t_top: lI of steps t_top + d
     const int64_t t_top = p.t_first + p.len - 1;
@@ -269,10 +274,7 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
             s_lI[i] = lIt;
             s_mn[i] = (uint8_t)((f >> 1) & 1u);
             win[tD * ws + i] = lIt;
-            if (g == 0) {
-                p.gN[gi] += (double)lIt;
-                __stcg(&p.lring[(size_t)((uint32_t)t & (kRing - 1)) * n + gi], lIt);
-            }
+            if (g == 0) s_gN[i] += (double)lIt;
         }
         __syncthreads();
         // the near part of step t - 1's gather (it reads step t), its partials
@@ -287,6 +289,14 @@ k_adjoint_part(const __grid_constant__ AdjPartParams p) {
             p.lu[lo + i] = s_lu[i];
             p.lI[lo + i] = s_lI[i];
             p.mnext[lo + i] = s_mn[i];
+            p.gN[lo + i] = s_gN[i];
+        }
+        // the lI ring of the next launch (the segment before): steps t_first
+        // .. t_first + R - 2, which the window holds now
+        for (uint32_t k = tid; k < (R - 1) * nc; k += kApThreads) {
+            const uint32_t d = k / nc, i = k - d * nc;
+            const int64_t tt = p.t_first + d;
+            p.lring[(size_t)(tt & (kRing - 1)) * n + lo + i] = win[(uint32_t)(tt % R) * ws + i];
         }
     }
 }
@@ -505,7 +515,7 @@ int adjoint_part_plan(int n, int n_pop, const int32_t* pop_start, int n_part, co
     }
     const size_t ws = ((size_t)ncmax + 31) / 32 * 32;
     const size_t smem = img_max * 4 + (size_t)R * ws * 4 + (size_t)2 * (span_max * kMaxPop * kWCodes + 4) * 4 +
-                        (size_t)ncmax * 8 + (size_t)max_lg * 32 * 4 + (size_t)ncmax;
+                        (size_t)ncmax * 8 + (size_t)max_lg * 32 * 4 + 8 + (size_t)ncmax * 8 + (size_t)ncmax;
     if (smem > (size_t)optin) return 1;
     plan->grid = n_part * G;
     plan->groups = G;
