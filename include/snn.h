@@ -265,13 +265,14 @@ int snn_export_network(snn_net* net, uint64_t* row_ptr_host, uint32_t* words_hos
  * step 6 does for the spikes of step t (Sec. 3.1.2: row fetch, word decode,
  * buffer add).  spikes_dev: device array of n_spikes neuron ids (duplicates
  * allowed).  tiling 0: one warp per spike; 1: one CTA per spike row; 2: one
- * CTA per partition, through the partition slots as in snn_step (the ring
- * slice in shared memory when it fits); 3: one CTA per partition reading
- * exactly its segment of each row (the entries between the partition
- * offsets), the weights and, when it fits, the ring slice in shared memory;
- * it reads a pre-decoded copy of the rows (4 bytes per synapse, weight-table
- * index and ring-cell offset), allocated and built on its first use (its
- * 19-bit offsets cover 64 slots of the largest partition a network can have);
+ * CTA per partition, through the step kernel's delivery (each spike's run of
+ * the pre-decoded rows onto the partition; the ring slice in shared memory
+ * when it fits); 3: one CTA per partition reading exactly its run of each
+ * row (the pre-decoded entries between the partition offsets: 4 bytes per
+ * synapse, weight-table index and ring-cell offset, built with the network),
+ * with the weights and, when they fit, the sums of the ring slots the list
+ * can reach (t + 1 .. t + the longest delay) in shared memory, added into the
+ * ring at the end (else straight into the ring in global memory);
  * 4: clusters of 8 CTAs,
  * one partition's ring slice in each CTA's shared memory, every row read once
  * per cluster and added through distributed shared memory
