@@ -64,7 +64,7 @@ TILING_NAMES = ["warp", "block", "partition", "words", "cluster", "stream"]   # 
 # dram__bytes_write.sum of one 2000-step launch that delivered 19,040.77
 # events per step); the full-size launch's traffic is taken as this figure
 # times its events (re-measure whenever k_step changes)
-K_STEP_DRAM_BYTES_PER_EVENT = (108.134400e6 + 3.530752e6) / (2000 * 19040.7745)
+K_STEP_DRAM_BYTES_PER_EVENT = (108.322560e6 + 3.360512e6) / (2000 * 19040.7745)
 K_STEP_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 2000-step "
                          "k_step launch at scale 0.4 (30,868 neurons, 192 MB of rows): 2.93 B "
                          "per synaptic event, times this launch's events; a lower estimate at "

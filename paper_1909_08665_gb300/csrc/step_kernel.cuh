@@ -53,14 +53,20 @@ constexpr uint32_t kStatusRasterOverflow = 2u;
 constexpr int kInline = 7;              // ids read together with a message header (64 B)
 // A warp takes BATCH spikes at once and loads the first 32 WAVE entries of
 // each of their runs in one wave (runs: mean 26 entries at scale 1 and 4,
-// rarely above 96).  Measured at full size (one neuron per thread), 3 x 3 is
-// fastest (3.00 us per step; 4 x 4: 3.14, 2 x 3: 3.08, 3 x 2: 3.24, 2 x 2:
-// 3.21): 16 warps x 3 spikes cover a mean step (46 spikes) in one round.  At
-// 4x (4 neurons per thread, 177 spikes per step) 8 x 3 is (14.3 us; 4 x 4:
-// 14.5, 3 x 3: 15.9, 6 x 4: 16.0, 8 x 4: 16.4).
+// rarely above 96).  At full size (one neuron per thread) the spikes are
+// dealt round-robin over the warps and each warp loads its next batch before
+// the adds of the current one; measured that way, 2 x 3 is fastest (2.566 us
+// per step; 3 x 3: 2.618, 2 x 2: 2.658, 4 x 3: 2.695, 4 x 2: 2.725, 1 x 3:
+// 2.754; two batches ahead, 2 x 3: 2.657, 1 x 3: 2.779), against 2.711 for
+// 3 x 3 in contiguous batches without the early load, the fastest shape of
+// those (earlier in the kernel's history 3.00 us; 4 x 4: 3.14, 2 x 3: 3.08,
+// 3 x 2: 3.24, 2 x 2: 3.21).  At 4x
+// (4 neurons per thread, 177 spikes per step; contiguous batches, loaded one
+// at a time: the registers of that variant are spent) 8 x 3 is fastest
+// (14.3 us; 4 x 4: 14.5, 3 x 3: 15.9, 6 x 4: 16.0, 8 x 4: 16.4).
 template <int NPT>
 struct BatchShape {
-    static constexpr int kSpikes = NPT == 1 ? 3 : 8;
+    static constexpr int kSpikes = NPT == 1 ? 2 : 8;
     static constexpr int kWave = 3;
 };
 constexpr uint32_t kPopWords = kMaxPop * kWCodes;   // weight-table entries per target population
@@ -164,7 +170,11 @@ __device__ inline bool poll_word(const StepParams& sp, const unsigned long long*
 // s_w (table rows from population p_lo on, wbase = p_lo * kPopWords), is
 // added at ((tb mod 64) * ncmax + offset) wrapped into the 64-slot ring.  Each
 // lane loads entries lane + 32 h (h < kRunWave) of all the batch's runs before the
-// first add (all loads in flight at once); longer runs finish in a loop.
+// first add (all loads in flight at once); longer runs finish in a loop.  In
+// the pipelined shape (PIPE) warp w's batch of round r holds the list's
+// spikes r kStride + w + k kWarps (k < kBatchSpikes), so a short list spreads
+// over all warps, and the next round's batch is loaded before this one's
+// adds; otherwise a batch is kBatchSpikes consecutive spikes.
 // ---------------------------------------------------------------------------
 // SAT: the networks whose input can leave the int32 range also count, per
 // ring cell, the net number of times its int32 sum wrapped around (+1 past
@@ -199,20 +209,37 @@ __device__ __forceinline__ void deliver_batches(const StepParams& sp, const uint
     const int32_t R = kRing * sp.ncmax;                  // ring words of this CTA
     const int32_t base_t = (int32_t)(((uint32_t)tb & (kRing - 1)) * (uint32_t)sp.ncmax);
     const uint32_t* pre = sp.pre;
-    for (uint32_t g0 = (uint32_t)warp * kBatchSpikes; g0 < m; g0 += (uint32_t)kWarps * kBatchSpikes) {
-        uint32_t rb[kBatchSpikes], rl[kBatchSpikes];
-        uint32_t ev[kBatchSpikes][kRunWave];
+    // PIPE: the warp's next batch is loaded before this one's adds, so its
+    // round trip overlaps them (steps with more than kStride spikes); only
+    // where the registers allow it (the one-neuron-per-thread shape)
+    constexpr bool PIPE = kBatchSpikes * kRunWave <= 9;
+    // run bounds and first-wave entries of the batch whose first spike is
+    // list position g0 (nothing past m is read)
+    auto load = [&](uint32_t g0, uint32_t (&rb)[kBatchSpikes], uint32_t (&rl)[kBatchSpikes],
+                    uint32_t (&ev)[kBatchSpikes][kRunWave]) {
 #pragma unroll
         for (int k = 0; k < kBatchSpikes; ++k) {
-            const bool ok = g0 + (uint32_t)k < m;
-            rb[k] = ok ? s_rb[g0 + k] : 0u;
-            rl[k] = ok ? s_rl[g0 + k] : 0u;
+            const uint32_t i = g0 + (uint32_t)k * (PIPE ? (uint32_t)kWarps : 1u);
+            const bool ok = i < m;
+            rb[k] = ok ? s_rb[i] : 0u;
+            rl[k] = ok ? s_rl[i] : 0u;
 #pragma unroll
             for (int h = 0; h < kRunWave; ++h) {
                 const uint32_t e = (uint32_t)lane + 32u * (uint32_t)h;
                 ev[k][h] = e < rl[k] ? __ldg(pre + ((size_t)rb[k] + e)) : 0u;
             }
         }
+    };
+    constexpr uint32_t kStride = (uint32_t)kWarps * kBatchSpikes;
+    uint32_t g0 = (uint32_t)warp * (PIPE ? 1u : (uint32_t)kBatchSpikes);
+    uint32_t rb[kBatchSpikes], rl[kBatchSpikes];
+    uint32_t ev[kBatchSpikes][kRunWave];
+    if (PIPE) load(g0, rb, rl, ev);
+    for (; g0 < m; g0 += kStride) {
+        uint32_t nrb[kBatchSpikes], nrl[kBatchSpikes];
+        uint32_t nev[kBatchSpikes][kRunWave];
+        if (PIPE) load(g0 + kStride, nrb, nrl, nev);
+        else load(g0, rb, rl, ev);
 #pragma unroll
         for (int k = 0; k < kBatchSpikes; ++k) {
 #pragma unroll
@@ -233,6 +260,15 @@ __device__ __forceinline__ void deliver_batches(const StepParams& sp, const uint
             }
             atomicAdd(&s_cnt[0], ev_sum);
             atomicAdd(&s_cnt[1], busy);
+        }
+        if (PIPE) {
+#pragma unroll
+            for (int k = 0; k < kBatchSpikes; ++k) {
+                rb[k] = nrb[k];
+                rl[k] = nrl[k];
+#pragma unroll
+                for (int h = 0; h < kRunWave; ++h) ev[k][h] = nev[k][h];
+            }
         }
     }
 }
